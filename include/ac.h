@@ -1,0 +1,319 @@
+/*
+ * ac.h - C-ABI of the GB300 Aho-Corasick DNA scan (libac.so).
+ *
+ * The problem statement follows the paper (Sec. IV.B, the matching module it
+ * builds on): given an array of keyword strings and a text, report every
+ * keyword occurrence and its position; Aho-Corasick does this in a single
+ * pass over the text (Sec. I, Sec. III.A). The machine is built in two
+ * stages (Sec. III.A): the goto/failure/output machine from the keywords,
+ * then one pass over the text. This library flattens the machine into a full
+ * deterministic transition table over {A,C,G,T} (the failure transitions are
+ * folded in at build time, so the scan takes exactly one table lookup per
+ * base) and runs the pass on the GPU.
+ *
+ * Conventions (the paper leaves them open):
+ *   - an occurrence is (start, pattern_id, text_id); start is the 0-based
+ *     offset of the keyword's first base; pattern_id is the 0-based index in
+ *     the caller's keyword array; duplicate keywords are separate ids and are
+ *     all reported; overlapping occurrences are all reported (Fig. 2);
+ *   - the alphabet is exactly A, C, G, T (lower case only with
+ *     AC_BUILD_FOLD_CASE / AC_SCAN_FOLD_CASE); any other byte is an error;
+ *   - occurrences come out in no particular order; (text_id, start,
+ *     pattern_id) is unique, so a sort on that key gives the canonical form.
+ *
+ * General rules for every call:
+ *   - every call returns an ac_status (0 = AC_OK, negative = error) and never
+ *     throws across the ABI; ac_status_str() names the code;
+ *   - "device pointer" means memory of the current CUDA device; "host
+ *     pointer" means ordinary (pageable or pinned) host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued on it; calls that must return a count
+ *     synchronise that stream only;
+ *   - the library owns ac_dfa and ac_server objects; the caller owns every
+ *     text and result buffer it passes in and keeps it alive for the call;
+ *   - an ac_dfa is immutable after ac_build, so concurrent scans of one
+ *     ac_dfa from several host threads / streams are safe.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+
+enum ac_status_code {
+    AC_OK = 0,
+    AC_ERR_INVALID_ARG = -1,   /* NULL pointer, bad size, misaligned buffer, bad option      */
+    AC_ERR_ALPHABET = -2,      /* a byte outside {A,C,G,T}; ac_result.bad_offset says where  */
+    AC_ERR_EMPTY_PATTERN = -3, /* a keyword of length 0                                      */
+    AC_ERR_TOO_LARGE = -4,     /* machine or text beyond the documented limits               */
+    AC_ERR_OOM = -5,           /* host or device allocation failed (nothing leaked)          */
+    AC_ERR_OVERFLOW = -6,      /* more occurrences than ac_result.capacity; n_matches and
+                                  counts are still exact, matches[0..capacity) valid          */
+    AC_ERR_CUDA = -7,          /* a CUDA runtime call failed                                 */
+    AC_ERR_TIMEOUT = -8,       /* a bounded wait ran out (serving)                           */
+    AC_ERR_BUSY = -9,          /* serving admission refused (over the device budget)         */
+    AC_ERR_NOT_FOUND = -10,    /* unknown ticket / slot                                      */
+    AC_ERR_NO_DEVICE = -11     /* the object lives on the host only (AC_BUILD_HOST_ONLY)     */
+};
+
+const char* ac_status_str(int status);
+
+/* ------------------------------------------------------------------ machine */
+
+typedef struct ac_dfa ac_dfa;
+
+enum ac_build_flags {
+    AC_BUILD_FOLD_CASE = 1u, /* accept a,c,g,t in keywords as A,C,G,T                          */
+    AC_BUILD_HOST_ONLY = 2u  /* build the tables on the host only (no GPU needed); such a dfa
+                                can be inspected with ac_dfa_tables but not scanned          */
+};
+
+typedef struct {
+    uint32_t flags; /* ac_build_flags */
+    uint32_t reserved;
+} ac_build_opts;
+
+/*
+ * ac_build - stage 1 of Sec. III.A: build the pattern matching machine.
+ *
+ * patterns[i] points to lens[i] bytes (not NUL-terminated) of keyword i, for
+ * i < n_patterns. All host memory, read only during the call.
+ * Builds goto (a trie), failure (breadth first) and output (own keywords
+ * plus the output of the failure state), then the full transition table
+ * delta[s][c], c in {A=0,C=1,G=2,T=3}, with states renumbered breadth first
+ * (so shallow, frequently visited states have small ids). Unless
+ * AC_BUILD_HOST_ONLY is set the tables are copied to the current device
+ * (synchronously) and the returned dfa is ready to scan.
+ * Errors: AC_ERR_INVALID_ARG (NULL pointers, n_patterns == 0),
+ * AC_ERR_EMPTY_PATTERN, AC_ERR_ALPHABET (*out untouched), AC_ERR_TOO_LARGE
+ * (more than 2^27 states), AC_ERR_OOM, AC_ERR_CUDA.
+ */
+int ac_build(const char* const* patterns, const uint32_t* lens, uint32_t n_patterns,
+             const ac_build_opts* opts /* nullable */, ac_dfa** out);
+
+/* Frees the dfa and its device tables (synchronises the device first). NULL is a no-op. */
+void ac_free(ac_dfa* dfa);
+
+typedef struct {
+    uint32_t n_states;     /* S                                                   */
+    uint32_t n_patterns;   /* P                                                   */
+    uint32_t max_len;      /* L_max: longest keyword                              */
+    uint32_t min_len;      /* shortest keyword                                    */
+    uint32_t max_depth;    /* deepest state (= max_len)                           */
+    uint32_t on_device;    /* 1 when the tables are on the device                 */
+    uint64_t table_bytes;  /* 16 * S: the transition table                        */
+    uint64_t out_entries;  /* total size of all output sets                       */
+    uint64_t device_bytes; /* all device memory held by the dfa                   */
+    double build_ms;       /* host time of the build (construction + upload)      */
+} ac_dfa_info_t;
+
+int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
+
+/* Read-only views of the host copies of the tables (valid until ac_free).
+ *   delta[4*s + c]: bits 0-30 the next state, bit 31 set when the next state
+ *                   has a non-empty output set;
+ *   out_off[S+1], out_pid[out_entries]: output set of s is
+ *                   out_pid[out_off[s] .. out_off[s+1]);
+ *   pat_len[P], pat_state[P]: keyword length and the state where it ends;
+ *   depth[S]: distance of each state from the root;
+ *   fail[S]: failure state of each state (breadth-first ids). */
+typedef struct {
+    const uint32_t* delta;
+    const uint32_t* out_off;
+    const uint32_t* out_pid;
+    const uint32_t* pat_len;
+    const uint32_t* pat_state;
+    const uint32_t* depth;
+    const uint32_t* fail;
+} ac_dfa_tables_t;
+
+int ac_dfa_tables(const ac_dfa* dfa, ac_dfa_tables_t* out);
+
+/* ------------------------------------------------------------------- texts */
+
+enum ac_encoding {
+    AC_TEXT_ASCII = 0,  /* one byte per base, n_bases bytes                              */
+    AC_TEXT_PACKED2 = 1 /* 2 bits per base, A=0 C=1 G=2 T=3, 16 bases per little-endian
+                           uint32 word, base j in bits 2*(j%16).. of word j/16;
+                           ceil(n_bases/16) words; the pointer must be 16-byte aligned   */
+};
+
+typedef struct {
+    const void* data;  /* the bases, see ac_encoding (may be NULL when n_bases == 0)    */
+    uint64_t n_bases;  /* number of bases                                                */
+    int32_t encoding;  /* ac_encoding                                                    */
+    int32_t on_device; /* 1: data is a device pointer, 0: host pointer                   */
+} ac_text;
+
+/* ------------------------------------------------------------------ results */
+
+typedef struct {
+    uint64_t pos;        /* 0-based start of the occurrence in its text             */
+    uint32_t pattern_id; /* index into the keyword array given to ac_build          */
+    uint32_t text_id;    /* ac_scan_opts.text_id, or the text's index in a batch    */
+} ac_match;              /* 16 bytes */
+
+typedef struct {
+    ac_match* matches;   /* capacity entries, or NULL with capacity 0 (counts only) */
+    uint64_t capacity;   /* entries available at matches                            */
+    uint64_t n_matches;  /* out: exact number of occurrences (also on overflow)      */
+    uint64_t* counts;    /* [n_patterns] out: occurrences per keyword, or NULL       */
+    int32_t on_device;   /* 1: matches/counts are device pointers, 0: host pointers  */
+    int32_t reserved;
+    uint64_t bad_offset; /* out: first invalid base on AC_ERR_ALPHABET, else ~0      */
+} ac_result;
+
+/* ------------------------------------------------------------------- scans */
+
+enum ac_scan_flags {
+    AC_SCAN_FOLD_CASE = 1u /* ASCII text: accept a,c,g,t as A,C,G,T */
+};
+
+typedef struct {
+    uint64_t range_begin; /* owned end positions [range_begin, range_end): only
+                             occurrences ending there are reported; the scan
+                             reads max(0, range_begin - (L_max - 1)) onwards.   */
+    uint64_t range_end;   /* 0 = n_bases                                        */
+    uint32_t chunk;       /* bases owned per GPU chunk; 0 = tuned                */
+    uint32_t threads;     /* threads per block (64..1024, multiple of 32); 0 = tuned */
+    uint32_t interleave;  /* chunks walked per thread: 1, 2, 4 or 8; 0 = tuned  */
+    int32_t hot_states;   /* states staged in shared memory: -1 = tuned,
+                             0..S = exactly that many (breadth-first prefix)    */
+    uint32_t flags;       /* ac_scan_flags                                      */
+    uint32_t text_id;     /* copied into every ac_match.text_id (ac_scan only)  */
+} ac_scan_opts;
+
+/* Timing and launch shape of the last scan, filled when requested. */
+typedef struct {
+    float total_ms;      /* device time of the whole call (events on the stream)   */
+    float scan_ms;       /* device time of the scan kernel                         */
+    float pack_ms;       /* device time of the ASCII pack kernel (0 if packed)     */
+    float counts_ms;     /* device time of the count kernel                        */
+    uint32_t chunk, threads, interleave, hot_states, grid, blocks_per_sm;
+    uint64_t bases_walked; /* owned bases plus halo re-reads                       */
+} ac_scan_stats;
+
+/*
+ * ac_pack - ASCII bases to the 2-bit packed encoding on the device (the
+ * encoding step in front of the scan). ascii: device pointer to n bytes;
+ * packed: device pointer to ceil(n/16) words, 16-byte aligned. Lower case is
+ * accepted only with AC_SCAN_FOLD_CASE in flags. Synchronises the stream.
+ * On a byte outside the alphabet returns AC_ERR_ALPHABET with *bad_offset =
+ * the first such offset (else *bad_offset = ~0).
+ */
+int ac_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, uint32_t flags, uint64_t* bad_offset,
+            void* stream);
+
+/*
+ * ac_scan - stage 2 of Sec. III.A over one text: one pass, every occurrence
+ * whose end lies in the owned range (see ac_scan_opts) and per-keyword counts.
+ *
+ * Writes min(n_matches, capacity) occurrences to result->matches (any order)
+ * and, if result->counts != NULL, the exact per-keyword counts. Texts and
+ * results may be on the host or the device (flags in ac_text / ac_result);
+ * host data is staged through stream-ordered device memory.
+ * Synchronises `stream` once (to learn n_matches).
+ * Errors: AC_ERR_INVALID_ARG, AC_ERR_NO_DEVICE, AC_ERR_ALPHABET (with
+ * bad_offset), AC_ERR_OVERFLOW (n_matches and counts exact; retry with
+ * capacity >= n_matches), AC_ERR_OOM, AC_ERR_CUDA.
+ * stats (nullable) receives the launch shape and device times.
+ */
+int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,
+            void* stream, ac_scan_stats* stats /* nullable */);
+
+/*
+ * ac_scan_batch - many independent texts in one persistent launch.
+ *
+ * texts[0..n_texts): each text is scanned on its own (no occurrence spans two
+ * texts); ac_match.text_id is the text's index. Work is split into chunks of
+ * every text and handed out to warps through a device work counter (work
+ * stealing), so uneven lengths do not leave the GPU idle. counts are summed
+ * over all texts. All texts must share one encoding and one location (host
+ * or device). opts->range_* and opts->text_id are ignored.
+ * Synchronises `stream` once. Errors as ac_scan.
+ */
+int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* result,
+                  const ac_scan_opts* opts /* nullable */, void* stream, ac_scan_stats* stats /* nullable */);
+
+/* -------------------------------------------------------------- batch plans
+ * A batch plan fixes a set of device-resident packed texts and a dfa, and
+ * captures the whole batched scan (counter reset, persistent scan, counts)
+ * into one CUDA graph; ac_batch_plan_run replays it. This removes the
+ * per-call host work and launch overhead for repeated batches. */
+
+typedef struct ac_batch_plan ac_batch_plan;
+
+/* texts: device-resident AC_TEXT_PACKED2 descriptors (host array of
+ * descriptors, read during the call); result buffers must be device
+ * pointers and stay valid while the plan lives. */
+int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* result,
+                         const ac_scan_opts* opts /* nullable */, void* stream, ac_batch_plan** out);
+/* Replays the graph on `stream`; when sync != 0 waits and fills
+ * result->n_matches (and returns AC_ERR_OVERFLOW as ac_scan does). */
+int ac_batch_plan_run(ac_batch_plan* plan, void* stream, int sync, ac_result* result);
+void ac_batch_plan_free(ac_batch_plan* plan);
+
+/* ---------------------------------------------------------------- autotune
+ * Times candidate launch shapes (chunk, threads, interleave, shared-memory
+ * states) on a sample of a device-resident packed text and returns the
+ * fastest in *best. Results are cached per (device, dfa size class, text
+ * size class) for the life of the process; AC_TUNE=off skips the trials
+ * and returns the built-in defaults. */
+int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opts* best, void* stream);
+
+/* ----------------------------------------------------------------- serving
+ * Continuous batching over several resident dfas. Requests (host texts) are
+ * admitted while the device budget allows, grouped per dfa, and launched as
+ * batched scans on a pool of streams while earlier work is still running;
+ * completed requests are returned to their waiters. Every request's result
+ * is exactly its stand-alone ac_scan result. */
+
+typedef struct ac_server ac_server;
+
+typedef struct {
+    uint64_t device_budget_bytes; /* texts + outputs in flight (dfas not counted); 0 = 40 GB */
+    uint32_t n_streams;           /* concurrent batches on the device; 0 = 4               */
+    uint32_t max_batch;           /* requests per launched batch; 0 = 256                  */
+    uint32_t max_queue;           /* waiting requests before submit returns BUSY; 0 = 1<<16 */
+    uint32_t match_capacity_per_base_x1000; /* output reservation: capacity = n*x/1000 + 1024; 0 = 64 */
+} ac_serve_opts;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, failed;
+    uint64_t bases_completed;
+    uint64_t batches_launched;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> results on the host   */
+    double busy_s;                          /* wall time with work in flight   */
+    double gbases_per_s;                    /* bases_completed / busy_s / 1e9  */
+} ac_serve_stats_t;
+
+int ac_serve_create(const ac_serve_opts* opts /* nullable */, ac_server** out);
+/* Makes dfa selectable by *slot. The server does not own the dfa: keep it
+ * alive until ac_serve_destroy. */
+int ac_serve_add_dfa(ac_server* srv, const ac_dfa* dfa, uint32_t* slot);
+/* Queues a scan of a HOST text (ASCII or packed) against dfa `slot`; the
+ * bases are copied during the call, so the caller may reuse its buffer.
+ * Returns AC_ERR_BUSY when the queue is full or the text alone exceeds the
+ * device budget. */
+int ac_serve_submit(ac_server* srv, uint32_t slot, const ac_text* text, uint64_t* ticket);
+/* Waits up to timeout_us (<0: forever) for a ticket. On completion copies
+ * the occurrences (with text_id 0) and the counts into the HOST buffers of
+ * result (on_device must be 0), sets n_matches, and forgets the ticket.
+ * Returns AC_ERR_TIMEOUT if not done in time, or AC_ERR_OVERFLOW with
+ * n_matches set when capacity is too small - in both cases the ticket stays
+ * valid and the call can be repeated - or the request's own error. */
+int ac_serve_wait(ac_server* srv, uint64_t ticket, ac_result* result, int64_t timeout_us);
+int ac_serve_stats(ac_server* srv, ac_serve_stats_t* out);
+/* Finishes in-flight work, then frees everything. */
+void ac_serve_destroy(ac_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

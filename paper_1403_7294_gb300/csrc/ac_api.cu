@@ -1,0 +1,760 @@
+// ac_api.cu - the C-ABI entry points of libac.so (see include/ac.h).
+//
+// Memory: the dfa's tables live in plain device allocations owned by the
+// ac_dfa. Per-call scratch (the per-state hit counters, the occurrence
+// counter, staging for host texts/results, the packed copy of an ASCII text)
+// comes from the device's stream-ordered pool (cudaMallocAsync on the
+// caller's stream, released with cudaFreeAsync), so concurrent scans of one
+// dfa never share scratch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ac_internal.h"
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return AC_OK;
+    if (e == cudaErrorMemoryAllocation) return AC_ERR_OOM;
+    return AC_ERR_CUDA;
+}
+
+// ---- host-side fault injection: AC_FAULT=oom@k makes the k-th device
+// allocation of the process (1-based) fail as if the device were full.
+std::mutex g_fault_mu;
+long g_alloc_count = 0;
+long g_fault_oom_at = -2;
+
+bool inject_oom() {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (g_fault_oom_at == -2) {
+        g_fault_oom_at = -1;
+        const char* f = std::getenv("AC_FAULT");
+        if (f && std::strncmp(f, "oom@", 4) == 0) g_fault_oom_at = std::atol(f + 4);
+    }
+    ++g_alloc_count;
+    return g_fault_oom_at > 0 && g_alloc_count == g_fault_oom_at;
+}
+
+cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (inject_oom()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (inject_oom()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+void keep_pool_memory() {
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(once[dev & 63], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;  // this process's pool keeps freed blocks for reuse
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    });
+}
+
+// A list of stream-ordered allocations released together at the end of a call.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    cudaError_t get(void** p, size_t bytes) {
+        cudaError_t e = dev_alloc_async(p, bytes, st);
+        if (e == cudaSuccess && *p) ptrs.push_back(*p);
+        return e;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+// pinned 32-byte landing pad per host thread for the small D2H reads
+unsigned long long* pinned_pad() {
+    static thread_local unsigned long long* pad = nullptr;
+    if (!pad) {
+        if (cudaMallocHost(&pad, 4 * sizeof(unsigned long long)) != cudaSuccess) pad = nullptr;
+    }
+    return pad;
+}
+
+struct Events {
+    bool on = false;
+    cudaEvent_t ev[8] = {};
+    cudaStream_t st = nullptr;
+    Events(bool enable, cudaStream_t s) : on(enable), st(s) {
+        if (on)
+            for (auto& e : ev) cudaEventCreate(&e);
+    }
+    void rec(int i) {
+        if (on) cudaEventRecord(ev[i], st);
+    }
+    float ms(int a, int b) {
+        float v = 0.f;
+        if (on) cudaEventElapsedTime(&v, ev[a], ev[b]);
+        return v;
+    }
+    ~Events() {
+        if (on)
+            for (auto& e : ev) cudaEventDestroy(e);
+    }
+};
+
+uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ status
+
+extern "C" const char* ac_status_str(int s) {
+    switch (s) {
+        case AC_OK: return "ok";
+        case AC_ERR_INVALID_ARG: return "invalid argument";
+        case AC_ERR_ALPHABET: return "byte outside {A,C,G,T}";
+        case AC_ERR_EMPTY_PATTERN: return "empty keyword";
+        case AC_ERR_TOO_LARGE: return "too large";
+        case AC_ERR_OOM: return "out of memory";
+        case AC_ERR_OVERFLOW: return "occurrence buffer too small (counts exact)";
+        case AC_ERR_CUDA: return "CUDA error";
+        case AC_ERR_TIMEOUT: return "timed out";
+        case AC_ERR_BUSY: return "busy (admission refused)";
+        case AC_ERR_NOT_FOUND: return "not found";
+        case AC_ERR_NO_DEVICE: return "object has no device tables";
+        default: return "unknown status";
+    }
+}
+
+// ------------------------------------------------------------------- build
+
+extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint32_t n_patterns,
+                        const ac_build_opts* opts, ac_dfa** out) {
+    if (!out || !patterns || !lens || n_patterns == 0) return AC_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint32_t flags = opts ? opts->flags : 0u;
+    ac_dfa* d = new (std::nothrow) ac_dfa();
+    if (!d) return AC_ERR_OOM;
+    int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0, &d->host, nullptr);
+    if (rc != AC_OK) {
+        delete d;
+        return rc;
+    }
+    if (!(flags & AC_BUILD_HOST_ONLY)) {
+        const HostTables& h = d->host;
+        cudaGetDevice(&d->device);
+        struct Up {
+            uint32_t** dst;
+            const std::vector<uint32_t>* src;
+        } ups[] = {{&d->d_delta, &h.delta}, {&d->d_out_off, &h.out_off}, {&d->d_out_pid, &h.out_pid},
+                   {&d->d_pat_len, &h.pat_len}};
+        cudaError_t e = cudaSuccess;
+        for (auto& u : ups) {
+            const size_t bytes = std::max<size_t>(u.src->size(), 1) * sizeof(uint32_t);
+            e = dev_alloc((void**)u.dst, bytes);
+            if (e != cudaSuccess) break;
+            d->device_bytes += bytes;
+            if (!u.src->empty()) e = cudaMemcpy(*u.dst, u.src->data(), u.src->size() * 4, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) {
+            ac_free(d);
+            return cuda_status(e);
+        }
+        d->on_device = true;
+    }
+    d->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = d;
+    return AC_OK;
+}
+
+extern "C" void ac_free(ac_dfa* d) {
+    if (!d) return;
+    if (d->d_delta || d->d_out_off || d->d_out_pid || d->d_pat_len) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (d->device >= 0) cudaSetDevice(d->device);
+        cudaDeviceSynchronize();
+        cudaFree(d->d_delta);
+        cudaFree(d->d_out_off);
+        cudaFree(d->d_out_pid);
+        cudaFree(d->d_pat_len);
+        cudaSetDevice(cur);
+    }
+    delete d;
+}
+
+extern "C" int ac_dfa_info(const ac_dfa* d, ac_dfa_info_t* o) {
+    if (!d || !o) return AC_ERR_INVALID_ARG;
+    const HostTables& h = d->host;
+    o->n_states = h.n_states;
+    o->n_patterns = h.n_patterns;
+    o->max_len = h.max_len;
+    o->min_len = h.min_len;
+    o->max_depth = h.max_depth;
+    o->on_device = d->on_device ? 1u : 0u;
+    o->table_bytes = (uint64_t)h.n_states * 16;
+    o->out_entries = h.out_pid.size();
+    o->device_bytes = d->device_bytes;
+    o->build_ms = d->build_ms;
+    return AC_OK;
+}
+
+extern "C" int ac_dfa_tables(const ac_dfa* d, ac_dfa_tables_t* o) {
+    if (!d || !o) return AC_ERR_INVALID_ARG;
+    const HostTables& h = d->host;
+    o->delta = h.delta.data();
+    o->out_off = h.out_off.data();
+    o->out_pid = h.out_pid.data();
+    o->pat_len = h.pat_len.data();
+    o->pat_state = h.pat_state.data();
+    o->depth = h.depth.data();
+    o->fail = h.fail.data();
+    return AC_OK;
+}
+
+// -------------------------------------------------------------------- pack
+
+extern "C" int ac_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, uint32_t flags, uint64_t* bad_offset,
+                       void* stream) {
+    if (bad_offset) *bad_offset = ~0ull;
+    if (n == 0) return AC_OK;
+    if (!ascii || !packed || (reinterpret_cast<uintptr_t>(packed) & 15)) return AC_ERR_INVALID_ARG;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* d_bad = nullptr;
+    Scratch sc(st);
+    cudaError_t e = sc.get((void**)&d_bad, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemsetAsync(d_bad, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = ac_launch_pack(ascii, n, packed, (flags & AC_SCAN_FOLD_CASE) != 0, d_bad, stream);
+    if (rc) return cuda_status((cudaError_t)rc);
+    unsigned long long* pad = pinned_pad();
+    if (!pad) return AC_ERR_OOM;
+    e = cudaMemcpyAsync(pad, d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (bad_offset) *bad_offset = pad[0];
+    return pad[0] == ~0ull ? AC_OK : AC_ERR_ALPHABET;
+}
+
+// ----------------------------------------------------------------- shapes
+
+ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts* o) {
+    const DeviceProps& p = ac_device_props();
+    const HostTables& h = dfa->host;
+    ScanShape sh;
+    if (!(o && o->chunk && o->threads && o->interleave && o->hot_states >= 0)) {
+        ScanShape tuned;
+        if (ac_tuned_lookup(dfa, owned, &tuned)) sh = tuned;
+    }
+    if (o && o->threads) sh.threads = o->threads;
+    if (o && o->interleave) sh.interleave = o->interleave;
+    if (o && o->hot_states >= 0) sh.hot = (uint32_t)o->hot_states;
+    if (o && o->chunk) sh.chunk = o->chunk;
+    if (!sh.interleave) sh.interleave = 4;
+    if (!sh.threads) sh.threads = ac_max_threads(sh.interleave);
+    sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave));
+    const uint32_t max_hot = ac_max_hot_states();
+    if (!(o && o->hot_states >= 0) && !sh.hot) sh.hot = std::min(h.n_states, max_hot);
+    sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
+    sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
+    const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
+    if (!sh.chunk) {
+        const uint64_t halo = h.max_len ? h.max_len - 1 : 0;
+        uint64_t c = round_up((owned + lanes - 1) / std::max<uint64_t>(lanes, 1), 64);
+        c = std::max<uint64_t>(c, std::max<uint64_t>(256, round_up(8 * halo, 64)));
+        sh.chunk = (uint32_t)std::min<uint64_t>(c, 1u << 30);
+    }
+    const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
+    const uint64_t per_block = (uint64_t)sh.threads * sh.interleave;
+    const uint64_t want = std::max<uint64_t>(1, (n_chunks + per_block - 1) / per_block);
+    sh.grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)p.sms * sh.blocks_per_sm);
+    return sh;
+}
+
+namespace {
+
+bool valid_shape_opts(const ac_scan_opts* o) {
+    if (!o) return true;
+    if (o->threads && (o->threads < 32 || o->threads > 1024 || o->threads % 32)) return false;
+    if (o->interleave && o->interleave != 1 && o->interleave != 2 && o->interleave != 4 && o->interleave != 8)
+        return false;
+    if (o->threads && o->threads > ac_max_threads(o->interleave ? o->interleave : 4)) return false;
+    return true;
+}
+
+size_t text_bytes(const ac_text& t) {
+    return t.encoding == AC_TEXT_ASCII ? (size_t)t.n_bases : (size_t)((t.n_bases + 15) / 16) * 4;
+}
+
+// Finishes a scan: reads n_matches and the bad offset, copies host results.
+int finish(cudaStream_t st, const unsigned long long* d_counter, const unsigned long long* d_bad,
+           ac_result* r, const ac_match* d_matches, const unsigned long long* d_counts, uint32_t n_pat) {
+    unsigned long long* pad = pinned_pad();
+    if (!pad) return AC_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(pad, d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && d_bad)
+        e = cudaMemcpyAsync(pad + 1, d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t nm = pad[0];
+    const uint64_t bad = d_bad ? pad[1] : ~0ull;
+    r->n_matches = nm;
+    r->bad_offset = bad;
+    if (bad != ~0ull) return AC_ERR_ALPHABET;
+    if (!r->on_device) {
+        const uint64_t k = std::min<uint64_t>(nm, r->capacity);
+        if (k) e = cudaMemcpyAsync(r->matches, d_matches, k * sizeof(ac_match), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && r->counts)
+            e = cudaMemcpyAsync(r->counts, d_counts, (size_t)n_pat * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return nm > r->capacity ? AC_ERR_OVERFLOW : AC_OK;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------- scan
+
+extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts, void* stream,
+                       ac_scan_stats* stats) {
+    if (!dfa || !text || !r) return AC_ERR_INVALID_ARG;
+    r->bad_offset = ~0ull;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    const uint64_t n = text->n_bases;
+    const uint64_t own_begin = opts ? opts->range_begin : 0;
+    const uint64_t own_end = (opts && opts->range_end) ? opts->range_end : n;
+    if (own_begin > own_end || own_end > n) return AC_ERR_INVALID_ARG;
+    if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
+        return AC_ERR_INVALID_ARG;
+    const HostTables& h = dfa->host;
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    Events ev(stats != nullptr, st);
+    Scratch sc(st);
+    cudaError_t e;
+    ev.rec(0);
+
+    // ---- text onto the device, packed
+    const uint32_t* words = nullptr;
+    const void* src = text->data;
+    if (!text->on_device && n) {
+        void* d_src = nullptr;
+        if ((e = sc.get(&d_src, round_up(text_bytes(*text), 16))) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(d_src, text->data, text_bytes(*text), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_status(e);
+        src = d_src;
+    }
+    unsigned long long* d_ctr = nullptr;  // [0] occurrences [1] cursor [2] bad offset [3] pad
+    unsigned long long* d_hits = nullptr;
+    if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
+    ev.rec(1);
+    if (text->encoding == AC_TEXT_ASCII && n) {
+        uint32_t* d_packed = nullptr;
+        if ((e = sc.get((void**)&d_packed, round_up((n + 15) / 16 * 4, 16))) != cudaSuccess) return cuda_status(e);
+        int rc = ac_launch_pack((const uint8_t*)src, n, d_packed, fold != 0, d_ctr + 2, stream);
+        if (rc) return cuda_status((cudaError_t)rc);
+        words = d_packed;
+    } else {
+        words = (const uint32_t*)src;
+    }
+    ev.rec(2);
+
+    // ---- outputs
+    ac_match* d_matches = r->matches;
+    unsigned long long* d_counts = (unsigned long long*)r->counts;
+    if (!r->on_device) {
+        if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
+        if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess)
+            return cuda_status(e);
+    }
+
+    // ---- the scan
+    const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
+    ScanArgs a;
+    a.delta = dfa->d_delta;
+    a.out_off = dfa->d_out_off;
+    a.out_pid = dfa->d_out_pid;
+    a.pat_len = dfa->d_pat_len;
+    a.n_states = h.n_states;
+    a.text = words;
+    a.n = n;
+    a.own_begin = own_begin;
+    a.own_end = own_end;
+    a.halo = h.max_len - 1;
+    a.text_id = opts ? opts->text_id : 0u;
+    a.matches = d_matches;
+    a.capacity = r->capacity;
+    a.counter = d_ctr;
+    a.hits = d_hits;
+    ev.rec(3);
+    int rc = ac_launch_scan(a, sh, stream);
+    if (rc) return cuda_status((cudaError_t)rc);
+    ev.rec(4);
+    if (d_counts) {
+        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
+        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, stream);
+        if (rc) return cuda_status((cudaError_t)rc);
+    }
+    ev.rec(5);
+    int status = finish(st, d_ctr, text->encoding == AC_TEXT_ASCII ? d_ctr + 2 : nullptr, r, d_matches, d_counts,
+                        h.n_patterns);
+    ev.rec(6);
+    if (stats) {
+        cudaEventSynchronize(ev.ev[6]);
+        stats->total_ms = ev.ms(0, 6);
+        stats->pack_ms = ev.ms(1, 2);
+        stats->scan_ms = ev.ms(3, 4);
+        stats->counts_ms = ev.ms(4, 5);
+        stats->chunk = sh.chunk;
+        stats->threads = sh.threads;
+        stats->interleave = sh.interleave;
+        stats->hot_states = sh.hot;
+        stats->grid = sh.grid;
+        stats->blocks_per_sm = sh.blocks_per_sm;
+        const uint64_t owned = own_end - own_begin;
+        const uint64_t n_chunks = owned ? (owned + sh.chunk - 1) / sh.chunk : 0;
+        stats->bases_walked = owned + n_chunks * (uint64_t)(h.max_len - 1);
+    }
+    return status;
+}
+
+// ------------------------------------------------------------------- batch
+
+namespace {
+
+struct BatchLayout {
+    std::vector<BatchText> texts;             // device pointers
+    std::vector<unsigned long long> prefix;   // [T+1]
+};
+
+// Shape for the persistent batched kernel: one wave of resident blocks.
+ScanShape batch_shape(const ac_dfa* dfa, uint64_t total, const ac_scan_opts* opts, uint32_t n_texts) {
+    ScanShape sh = ac_default_shape(dfa, total, opts);
+    const DeviceProps& p = ac_device_props();
+    if (!(opts && opts->chunk)) {
+        // enough chunks for every lane of the wave, at least 256 bases each
+        const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
+        const uint64_t halo = dfa->host.max_len ? dfa->host.max_len - 1 : 0;
+        uint64_t c = round_up(std::max<uint64_t>(1, total / std::max<uint64_t>(lanes, 1)), 64);
+        c = std::max<uint64_t>(c, std::max<uint64_t>(256, round_up(4 * halo, 64)));
+        sh.chunk = (uint32_t)std::min<uint64_t>(c, 1u << 20);
+    }
+    (void)n_texts;
+    sh.grid = (uint32_t)p.sms * sh.blocks_per_sm;
+    return sh;
+}
+
+int make_prefix(const std::vector<uint64_t>& lens, uint32_t chunk, std::vector<unsigned long long>* prefix) {
+    prefix->assign(lens.size() + 1, 0);
+    for (size_t i = 0; i < lens.size(); ++i) (*prefix)[i + 1] = (*prefix)[i] + (lens[i] + chunk - 1) / chunk;
+    return AC_OK;
+}
+
+}  // namespace
+
+extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* r,
+                             const ac_scan_opts* opts, void* stream, ac_scan_stats* stats) {
+    if (!dfa || !r || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
+    r->bad_offset = ~0ull;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    const HostTables& h = dfa->host;
+    const int enc = n_texts ? texts[0].encoding : AC_TEXT_PACKED2;
+    const int on_dev = n_texts ? texts[0].on_device : 1;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < n_texts; ++i) {
+        const ac_text& t = texts[i];
+        if (t.encoding != enc || t.on_device != on_dev) return AC_ERR_INVALID_ARG;
+        if (t.encoding != AC_TEXT_ASCII && t.encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+        if (t.n_bases && !t.data) return AC_ERR_INVALID_ARG;
+        if (t.on_device && t.encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(t.data) & 15))
+            return AC_ERR_INVALID_ARG;
+        total += t.n_bases;
+    }
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    Events ev(stats != nullptr, st);
+    Scratch sc(st);
+    cudaError_t e;
+    ev.rec(0);
+
+    unsigned long long* d_ctr = nullptr;
+    unsigned long long* d_hits = nullptr;
+    if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
+
+    // ---- every text onto the device, packed, each starting on a 64-base boundary
+    std::vector<BatchText> bt(n_texts);
+    std::vector<uint64_t> lens(n_texts);
+    for (uint32_t i = 0; i < n_texts; ++i) lens[i] = texts[i].n_bases;
+    ev.rec(1);
+    if (enc == AC_TEXT_PACKED2 && on_dev) {
+        for (uint32_t i = 0; i < n_texts; ++i) bt[i] = BatchText{(const uint32_t*)texts[i].data, lens[i]};
+    } else {
+        // staging: each text at a 64-base aligned slot in one buffer
+        std::vector<uint64_t> slot(n_texts + 1, 0);  // in bases
+        for (uint32_t i = 0; i < n_texts; ++i) slot[i + 1] = slot[i] + round_up(lens[i], 64);
+        const uint64_t all = slot[n_texts];
+        uint32_t* d_words = nullptr;
+        if ((e = sc.get((void**)&d_words, std::max<uint64_t>(all / 16 * 4, 16))) != cudaSuccess)
+            return cuda_status(e);
+        if (enc == AC_TEXT_PACKED2) {  // host packed texts: copy word ranges
+            for (uint32_t i = 0; i < n_texts; ++i)
+                if (lens[i] &&
+                    (e = cudaMemcpyAsync(d_words + slot[i] / 16, texts[i].data, (lens[i] + 15) / 16 * 4,
+                                         cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                    return cuda_status(e);
+        } else {  // ASCII: gather into one ASCII buffer padded with 'A', then one pack
+            uint8_t* d_ascii = nullptr;
+            if ((e = sc.get((void**)&d_ascii, std::max<uint64_t>(all, 16))) != cudaSuccess) return cuda_status(e);
+            if (all && (e = cudaMemsetAsync(d_ascii, 'A', all, st)) != cudaSuccess) return cuda_status(e);
+            for (uint32_t i = 0; i < n_texts; ++i)
+                if (lens[i] &&
+                    (e = cudaMemcpyAsync(d_ascii + slot[i], texts[i].data, lens[i],
+                                         on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) !=
+                        cudaSuccess)
+                    return cuda_status(e);
+            int rc = ac_launch_pack(d_ascii, all, d_words, fold != 0, d_ctr + 2, stream);
+            if (rc) return cuda_status((cudaError_t)rc);
+        }
+        for (uint32_t i = 0; i < n_texts; ++i) bt[i] = BatchText{d_words + slot[i] / 16, lens[i]};
+    }
+    ev.rec(2);
+
+    // ---- work items and the text table
+    ScanShape sh = batch_shape(dfa, total, opts, n_texts);
+    std::vector<unsigned long long> prefix;
+    make_prefix(lens, sh.chunk, &prefix);
+    BatchText* d_bt = nullptr;
+    unsigned long long* d_prefix = nullptr;
+    if ((e = sc.get((void**)&d_bt, std::max<size_t>(n_texts, 1) * sizeof(BatchText))) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = sc.get((void**)&d_prefix, prefix.size() * 8)) != cudaSuccess) return cuda_status(e);
+    if (n_texts &&
+        (e = cudaMemcpyAsync(d_bt, bt.data(), n_texts * sizeof(BatchText), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemcpyAsync(d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_status(e);
+    // the host vectors must outlive the async copies from pageable memory:
+    // pageable cudaMemcpyAsync returns after the source has been staged.
+
+    ac_match* d_matches = r->matches;
+    unsigned long long* d_counts = (unsigned long long*)r->counts;
+    if (!r->on_device) {
+        if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
+        if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    BatchArgs a;
+    a.delta = dfa->d_delta;
+    a.out_off = dfa->d_out_off;
+    a.out_pid = dfa->d_out_pid;
+    a.pat_len = dfa->d_pat_len;
+    a.n_states = h.n_states;
+    a.texts = d_bt;
+    a.item_prefix = d_prefix;
+    a.n_texts = n_texts;
+    a.n_items = prefix.back();
+    a.chunk = sh.chunk;
+    a.halo = h.max_len - 1;
+    a.matches = d_matches;
+    a.capacity = r->capacity;
+    a.counter = d_ctr;
+    a.hits = d_hits;
+    ev.rec(3);
+    int rc = ac_launch_batch(a, sh, stream);
+    if (rc) return cuda_status((cudaError_t)rc);
+    ev.rec(4);
+    if (d_counts) {
+        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
+        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, stream);
+        if (rc) return cuda_status((cudaError_t)rc);
+    }
+    ev.rec(5);
+    int status = finish(st, d_ctr, enc == AC_TEXT_ASCII ? d_ctr + 2 : nullptr, r, d_matches, d_counts, h.n_patterns);
+    ev.rec(6);
+    if (stats) {
+        cudaEventSynchronize(ev.ev[6]);
+        stats->total_ms = ev.ms(0, 6);
+        stats->pack_ms = ev.ms(1, 2);
+        stats->scan_ms = ev.ms(3, 4);
+        stats->counts_ms = ev.ms(4, 5);
+        stats->chunk = sh.chunk;
+        stats->threads = sh.threads;
+        stats->interleave = sh.interleave;
+        stats->hot_states = sh.hot;
+        stats->grid = sh.grid;
+        stats->blocks_per_sm = sh.blocks_per_sm;
+        stats->bases_walked = total + prefix.back() * (uint64_t)(h.max_len - 1);
+    }
+    return status;
+}
+
+// ------------------------------------------------------------ batch plans
+
+struct ac_batch_plan {
+    const ac_dfa* dfa = nullptr;
+    int device = 0;
+    uint32_t n_patterns = 0;
+    uint64_t capacity = 0;
+    BatchText* d_bt = nullptr;
+    unsigned long long* d_prefix = nullptr;
+    unsigned long long* d_ctr = nullptr;
+    unsigned long long* d_hits = nullptr;
+    unsigned long long* h_pad = nullptr;  // pinned: [0] n_matches
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" void ac_batch_plan_free(ac_batch_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_bt);
+    cudaFree(p->d_prefix);
+    cudaFree(p->d_ctr);
+    cudaFree(p->d_hits);
+    if (p->h_pad) cudaFreeHost(p->h_pad);
+    delete p;
+}
+
+extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* r,
+                                    const ac_scan_opts* opts, void* stream, ac_batch_plan** out) {
+    if (!dfa || !r || !out || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    if (!r->on_device || (r->capacity && !r->matches)) return AC_ERR_INVALID_ARG;
+    if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    const HostTables& h = dfa->host;
+    std::vector<BatchText> bt(n_texts);
+    std::vector<uint64_t> lens(n_texts);
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < n_texts; ++i) {
+        const ac_text& t = texts[i];
+        if (t.encoding != AC_TEXT_PACKED2 || !t.on_device) return AC_ERR_INVALID_ARG;
+        if ((t.n_bases && !t.data) || (reinterpret_cast<uintptr_t>(t.data) & 15)) return AC_ERR_INVALID_ARG;
+        bt[i] = BatchText{(const uint32_t*)t.data, t.n_bases};
+        lens[i] = t.n_bases;
+        total += t.n_bases;
+    }
+    ac_batch_plan* p = new (std::nothrow) ac_batch_plan();
+    if (!p) return AC_ERR_OOM;
+    p->dfa = dfa;
+    p->n_patterns = h.n_patterns;
+    p->capacity = r->capacity;
+    cudaGetDevice(&p->device);
+    ScanShape sh = batch_shape(dfa, total, opts, n_texts);
+    std::vector<unsigned long long> prefix;
+    make_prefix(lens, sh.chunk, &prefix);
+    cudaError_t e = cudaSuccess;
+    (void)stream;  // capture happens on a private stream; runs go to the caller's
+    auto fail = [&](cudaError_t err) {
+        ac_batch_plan_free(p);
+        return cuda_status(err);
+    };
+    if ((e = dev_alloc((void**)&p->d_bt, std::max<size_t>(n_texts, 1) * sizeof(BatchText))) != cudaSuccess)
+        return fail(e);
+    if ((e = dev_alloc((void**)&p->d_prefix, prefix.size() * 8)) != cudaSuccess) return fail(e);
+    if ((e = dev_alloc((void**)&p->d_ctr, 4 * 8)) != cudaSuccess) return fail(e);
+    if ((e = dev_alloc((void**)&p->d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost(&p->h_pad, 4 * 8)) != cudaSuccess) return fail(e);
+    if (n_texts && (e = cudaMemcpy(p->d_bt, bt.data(), n_texts * sizeof(BatchText), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpy(p->d_prefix, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+
+    BatchArgs a;
+    a.delta = dfa->d_delta;
+    a.out_off = dfa->d_out_off;
+    a.out_pid = dfa->d_out_pid;
+    a.pat_len = dfa->d_pat_len;
+    a.n_states = h.n_states;
+    a.texts = p->d_bt;
+    a.item_prefix = p->d_prefix;
+    a.n_texts = n_texts;
+    a.n_items = prefix.back();
+    a.chunk = sh.chunk;
+    a.halo = h.max_len - 1;
+    a.matches = r->matches;
+    a.capacity = r->capacity;
+    a.counter = p->d_ctr;
+    a.hits = p->d_hits;
+    unsigned long long* d_counts = (unsigned long long*)r->counts;
+
+    // capture on a private stream, then replay on any stream
+    if ((e = (cudaError_t)ac_prepare_batch(sh)) != cudaSuccess) return fail(e);
+    cudaStream_t cap = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    int rc = AC_OK;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(p->d_ctr, 0, 4 * 8, cap);
+        cudaMemsetAsync(p->d_hits, 0, (size_t)h.n_states * 8, cap);
+        rc = ac_launch_batch(a, sh, cap);
+        if (d_counts) {
+            cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, cap);
+            if (!rc) rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, p->d_hits, d_counts, cap);
+        }
+        cudaMemcpyAsync(p->h_pad, p->d_ctr, 8, cudaMemcpyDeviceToHost, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    cudaStreamDestroy(cap);
+    if (e == cudaSuccess && rc) e = (cudaError_t)rc;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) return fail(e);
+    *out = p;
+    return AC_OK;
+}
+
+extern "C" int ac_batch_plan_run(ac_batch_plan* p, void* stream, int sync, ac_result* r) {
+    if (!p) return AC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGraphLaunch(p->exec, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!sync) return AC_OK;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e);
+    const uint64_t nm = p->h_pad[0];
+    if (r) {
+        r->n_matches = nm;
+        r->bad_offset = ~0ull;
+    }
+    return nm > p->capacity ? AC_ERR_OVERFLOW : AC_OK;
+}

@@ -1,0 +1,178 @@
+// ac_builder.cpp - stage 1 of Sec. III.A on the host: the goto / failure /
+// output machine, then flattened into a full transition table over
+// {A,C,G,T} with states renumbered breadth first.
+//
+// goto:    a trie with a 4-way child array per state.
+// failure: breadth first; depth-1 states fail to the root; for a child u of r
+//          reached on a, fail(u) = goto(f, a) for the first f on r's failure
+//          chain (fail(r), fail(fail(r)), ..., root) that has an a-edge, else
+//          the root.
+// output:  the keywords ending at s plus output(fail(s)).
+// flatten: delta(s, a) = goto(s, a) if the edge exists, else delta(fail(s), a)
+//          (the root's missing edges loop to the root). Computed breadth
+//          first, so delta(fail(s), .) is final before s is visited. A scan
+//          over delta makes exactly one lookup per base and visits the same
+//          states as the paper's failure-following scan (Sec. III.A), which
+//          re-reads a character after each failure hop.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <new>
+
+#include "ac_internal.h"
+
+namespace {
+
+inline int base_code(uint8_t c, bool fold) {
+    switch (c) {
+        case 'A': return 0;
+        case 'C': return 1;
+        case 'G': return 2;
+        case 'T': return 3;
+        case 'a': return fold ? 0 : -1;
+        case 'c': return fold ? 1 : -1;
+        case 'g': return fold ? 2 : -1;
+        case 't': return fold ? 3 : -1;
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
+                  HostTables* t, uint32_t* bad_pattern) {
+    if (!patterns || !lens || n == 0 || !t) return AC_ERR_INVALID_ARG;
+    uint64_t total = 0;
+    for (uint32_t p = 0; p < n; ++p) {
+        if (lens[p] == 0) {
+            if (bad_pattern) *bad_pattern = p;
+            return AC_ERR_EMPTY_PATTERN;
+        }
+        if (!patterns[p]) return AC_ERR_INVALID_ARG;
+        for (uint32_t j = 0; j < lens[p]; ++j)
+            if (base_code((uint8_t)patterns[p][j], fold_case) < 0) {
+                if (bad_pattern) *bad_pattern = p;
+                return AC_ERR_ALPHABET;
+            }
+        total += lens[p];
+    }
+    try {
+        // ---- goto (trie), states in creation order
+        std::vector<int32_t> child;  // [S*4], -1 = no edge
+        child.reserve(std::min<uint64_t>(total + 1, AC_MAX_STATES) * 4);
+        child.assign(4, -1);
+        std::vector<std::vector<uint32_t>> own(1);
+        std::vector<uint32_t> pat_node(n);
+        uint32_t max_len = 0, min_len = UINT32_MAX;
+        for (uint32_t p = 0; p < n; ++p) {
+            int32_t s = 0;
+            for (uint32_t j = 0; j < lens[p]; ++j) {
+                int c = base_code((uint8_t)patterns[p][j], fold_case);
+                int32_t nx = child[(size_t)s * 4 + c];
+                if (nx < 0) {
+                    if (own.size() >= AC_MAX_STATES) return AC_ERR_TOO_LARGE;
+                    nx = (int32_t)own.size();
+                    child[(size_t)s * 4 + c] = nx;
+                    child.insert(child.end(), {-1, -1, -1, -1});
+                    own.emplace_back();
+                }
+                s = nx;
+            }
+            own[s].push_back(p);
+            pat_node[p] = (uint32_t)s;
+            max_len = std::max(max_len, lens[p]);
+            min_len = std::min(min_len, lens[p]);
+        }
+        const uint32_t S = (uint32_t)own.size();
+
+        // ---- breadth-first order (children visited A, C, G, T)
+        std::vector<uint32_t> order;  // bfs position -> creation id
+        order.reserve(S);
+        std::vector<uint32_t> depth_c(S, 0);
+        order.push_back(0);
+        for (size_t h = 0; h < order.size(); ++h) {
+            uint32_t r = order[h];
+            for (int c = 0; c < 4; ++c) {
+                int32_t u = child[(size_t)r * 4 + c];
+                if (u >= 0) {
+                    depth_c[u] = depth_c[r] + 1;
+                    order.push_back((uint32_t)u);
+                }
+            }
+        }
+        std::vector<uint32_t> bfs_id(S);
+        for (uint32_t i = 0; i < S; ++i) bfs_id[order[i]] = i;
+
+        // ---- failure + flattened delta in one breadth-first pass (creation ids).
+        // When r is visited, fail(r) was set by r's parent and the row of
+        // fail(r) (a shallower state, visited earlier) is final. For a child u of
+        // r on c, delta(fail(r), c) is exactly "follow r's failure chain until a
+        // c-edge exists, else the root", i.e. fail(u).
+        std::vector<uint32_t> fail_c(S, 0);
+        std::vector<uint32_t> delta_c((size_t)S * 4, 0);
+        for (uint32_t h = 0; h < S; ++h) {
+            uint32_t r = order[h];
+            for (int c = 0; c < 4; ++c) {
+                int32_t u = child[(size_t)r * 4 + c];
+                uint32_t via_fail = (r == 0) ? 0u : delta_c[(size_t)fail_c[r] * 4 + c];
+                if (u >= 0) {
+                    delta_c[(size_t)r * 4 + c] = (uint32_t)u;
+                    fail_c[u] = via_fail;  // depth-1 states: the root
+                } else {
+                    delta_c[(size_t)r * 4 + c] = via_fail;  // the root loops on itself
+                }
+            }
+        }
+
+        // ---- output sets: own(s) then output(fail(s)), breadth first
+        // (stored per breadth-first id as CSR)
+        std::vector<uint32_t> out_n(S, 0);
+        uint64_t E = 0;
+        for (uint32_t h = 0; h < S; ++h) {
+            uint32_t s = order[h];
+            out_n[s] = (uint32_t)own[s].size() + (s ? out_n[fail_c[s]] : 0u);
+            E += out_n[s];
+        }
+        if (E > 0xffffffffull) return AC_ERR_TOO_LARGE;
+
+        t->n_states = S;
+        t->n_patterns = n;
+        t->max_len = max_len;
+        t->min_len = min_len;
+        t->max_depth = depth_c[order[S - 1]];
+        t->out_off.assign((size_t)S + 1, 0);
+        for (uint32_t i = 0; i < S; ++i) t->out_off[i + 1] = t->out_off[i] + out_n[order[i]];
+        t->out_pid.assign(E, 0);
+        for (uint32_t i = 0; i < S; ++i) {
+            uint32_t s = order[i];
+            uint32_t w = t->out_off[i];
+            for (uint32_t p : own[s]) t->out_pid[w++] = p;
+            if (s) {
+                uint32_t f = bfs_id[fail_c[s]];  // already written: f < i
+                for (uint32_t k = t->out_off[f]; k < t->out_off[f + 1]; ++k) t->out_pid[w++] = t->out_pid[k];
+            }
+        }
+
+        // ---- renumber the flattened table to breadth-first ids, add the flag
+        t->delta.assign((size_t)S * 4, 0);
+        t->depth.assign(S, 0);
+        t->fail.assign(S, 0);
+        for (uint32_t i = 0; i < S; ++i) {
+            uint32_t s = order[i];
+            t->depth[i] = depth_c[s];
+            t->fail[i] = bfs_id[fail_c[s]];
+            for (int c = 0; c < 4; ++c) {
+                uint32_t nx = bfs_id[delta_c[(size_t)s * 4 + c]];
+                uint32_t flag = (t->out_off[nx + 1] > t->out_off[nx]) ? AC_FLAG : 0u;
+                t->delta[(size_t)i * 4 + c] = nx | flag;
+            }
+        }
+        t->pat_len.assign(lens, lens + n);
+        t->pat_state.resize(n);
+        for (uint32_t p = 0; p < n; ++p) t->pat_state[p] = bfs_id[pat_node[p]];
+    } catch (const std::bad_alloc&) {
+        return AC_ERR_OOM;
+    }
+    return AC_OK;
+}

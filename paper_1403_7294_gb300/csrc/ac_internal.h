@@ -1,0 +1,121 @@
+// ac_internal.h - shared between the translation units of libac.so only.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ac.h"
+
+// Transition entry: bits 0-30 next state, bit 31 "next state has output".
+static constexpr uint32_t AC_FLAG = 0x80000000u;
+static constexpr uint32_t AC_STATE_MASK = 0x7fffffffu;
+static constexpr uint32_t AC_MAX_STATES = 1u << 27;  // 16 B rows stay below 2 GiB
+
+struct HostTables {
+    uint32_t n_states = 0, n_patterns = 0, max_len = 0, min_len = 0, max_depth = 0;
+    std::vector<uint32_t> delta;      // [S*4]
+    std::vector<uint32_t> out_off;    // [S+1]
+    std::vector<uint32_t> out_pid;    // [E]
+    std::vector<uint32_t> pat_len;    // [P]
+    std::vector<uint32_t> pat_state;  // [P]
+    std::vector<uint32_t> depth;      // [S]
+    std::vector<uint32_t> fail;       // [S]
+};
+
+// Builds the flattened machine on the host. Returns an ac_status.
+int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
+                  HostTables* t, uint32_t* bad_pattern);
+
+struct ac_dfa {
+    HostTables host;
+    bool on_device = false;
+    int device = -1;
+    // device tables
+    uint32_t* d_delta = nullptr;
+    uint32_t* d_out_off = nullptr;
+    uint32_t* d_out_pid = nullptr;
+    uint32_t* d_pat_len = nullptr;
+    uint64_t device_bytes = 0;
+    double build_ms = 0.0;
+};
+
+// ------------------------------------------------------------ launch shapes
+
+struct ScanShape {
+    uint32_t chunk = 0;       // owned bases per chunk
+    uint32_t threads = 0;     // per block
+    uint32_t interleave = 0;  // chunks per thread
+    uint32_t hot = 0;         // states in shared memory
+    uint32_t grid = 0;        // blocks
+    uint32_t blocks_per_sm = 0;
+};
+
+struct DeviceProps {
+    int device = 0;
+    int sms = 0;
+    size_t smem_optin = 0;
+    size_t l2 = 0;
+};
+
+const DeviceProps& ac_device_props();
+
+// Kernel launchers (ac_kernels.cu). All return cudaError_t as int.
+struct ScanArgs {
+    const uint32_t* delta;
+    const uint32_t* out_off;
+    const uint32_t* out_pid;
+    const uint32_t* pat_len;
+    uint32_t n_states;
+    const uint32_t* text;   // packed words (16-byte aligned)
+    uint64_t n;             // bases in the text
+    uint64_t own_begin;     // owned end positions [own_begin, own_end)
+    uint64_t own_end;
+    uint32_t halo;          // L_max - 1
+    uint32_t text_id;
+    ac_match* matches;
+    uint64_t capacity;
+    unsigned long long* counter;  // [0] = occurrences
+    unsigned long long* hits;     // [S] flagged steps per state
+};
+
+int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold,
+                   unsigned long long* bad, void* stream);
+int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream);
+int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,
+                     const unsigned long long* hits, unsigned long long* counts, void* stream);
+// Largest block size the kernels are compiled for at a given interleave.
+uint32_t ac_max_threads(uint32_t interleave);
+// Largest number of states a scan block can stage in shared memory.
+uint32_t ac_max_hot_states();
+// Resident blocks per SM for a shape (occupancy query); 0 on error.
+uint32_t ac_blocks_per_sm(const ScanShape& sh);
+
+// Batched scan (ac_kernels.cu)
+struct BatchText {
+    const uint32_t* words;  // packed, 16-byte aligned
+    uint64_t n;             // bases
+};
+struct BatchArgs {
+    const uint32_t* delta;
+    const uint32_t* out_off;
+    const uint32_t* out_pid;
+    const uint32_t* pat_len;
+    uint32_t n_states;
+    const BatchText* texts;         // [T] device
+    const unsigned long long* item_prefix;  // [T+1] device: first work item of each text
+    uint32_t n_texts;
+    unsigned long long n_items;     // total chunks
+    uint32_t chunk;
+    uint32_t halo;
+    ac_match* matches;
+    uint64_t capacity;
+    unsigned long long* counter;    // [0] occurrences, [1] work cursor
+    unsigned long long* hits;
+};
+int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream);
+// Sets the batch kernel's shared-memory limit for a shape (call before graph capture).
+int ac_prepare_batch(const ScanShape& sh);
+
+// Default / tuned shape selection (ac_api.cu / ac_tune.cpp)
+ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned_bases, const ac_scan_opts* opts);
+bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out);

@@ -1,0 +1,483 @@
+// ac_kernels.cu - the GPU side of stage 2 of Sec. III.A: one pass of the
+// text over the flattened transition table.
+//
+// Layout in device memory
+//   delta    uint32[S][4]  row s = the 4 transitions of state s (16 B);
+//                          bits 0-30 next state, bit 31 "next state has output"
+//   out_off  uint32[S+1], out_pid uint32[E]: output(s) as CSR
+//   pat_len  uint32[P]
+//   text     uint32[ceil(n/16)] 2-bit packed, base j in bits 2*(j%16) of word j/16
+//
+// Work decomposition (the GPU form of the paper's "approach 1", Sec. IV.A):
+// the owned range is cut into chunks of `chunk` end positions; a chunk that
+// owns [lo, hi) walks from state 0 starting at a position <= lo - (L_max - 1)
+// (rounded down to a 64-base boundary, so text loads are aligned uint4s).
+// After reading position i the state is the longest suffix of text[..i] that
+// is a trie node; its length is at most L_max, so a walk that started at or
+// before i - (L_max - 1) is in the same state as a walk from the text start.
+// Every keyword ending at i is in output(state at i), and an occurrence has
+// one end position, so emitting only for ends in [lo, hi) reports every
+// occurrence exactly once.
+//
+// Each thread walks `I` chunks at once (independent dependency chains: their
+// table lookups are in flight together). States [0, hot) - the breadth-first
+// prefix of the machine, i.e. the shallow states most steps visit - are
+// staged in shared memory; the rest are read through L2 with an evict-last
+// policy, while the streamed text uses evict-first.
+//
+// Emission: a step whose entry has bit 31 set lands on a state with output.
+// The warp votes; when any lane hit, lanes expand their output sets, a warp
+// prefix sum (shuffles) assigns slots, one lane does a single atomicAdd for
+// the whole warp, and each lane writes its 16-byte occurrences. A per-state
+// hit counter feeds the exact per-keyword counts (kept exact on overflow).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ac_internal.h"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint32_t ld_table(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_text4(const uint32_t* p, uint64_t pol) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+// 64 bases starting at word w (w % 4 == 0); words past the end read as 0.
+__device__ __forceinline__ uint4 load_block(const uint32_t* text, uint64_t w, uint64_t nwords, uint64_t pol) {
+    if (w + 4 <= nwords) return ld_text4(text + w, pol);
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (w + 0 < nwords) v.x = text[w + 0];
+    if (w + 1 < nwords) v.y = text[w + 1];
+    if (w + 2 < nwords) v.z = text[w + 2];
+    return v;
+}
+
+struct Tables {
+    const uint32_t* __restrict__ delta;
+    const uint32_t* __restrict__ out_off;
+    const uint32_t* __restrict__ out_pid;
+    const uint32_t* __restrict__ pat_len;
+};
+
+struct Sink {
+    ac_match* __restrict__ matches;
+    uint64_t capacity;
+    unsigned long long* counter;
+    unsigned long long* hits;
+};
+
+// Warp-cooperative emission. Called by all 32 lanes (warp-uniform branch).
+__device__ __noinline__ void emit_warp(bool mine, uint32_t st, uint64_t end_pos, uint32_t text_id,
+                                       Tables tb, Sink sk) {
+    const int lane = threadIdx.x & 31;
+    uint32_t o0 = 0, k = 0;
+    if (mine) {
+        o0 = tb.out_off[st];
+        k = tb.out_off[st + 1] - o0;
+        atomicAdd(&sk.hits[st], 1ull);
+    }
+    uint32_t incl = k;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t v = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(sk.counter, (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31);
+    unsigned long long w = base + (incl - k);
+    for (uint32_t i = 0; i < k; ++i, ++w) {
+        if (w >= sk.capacity) break;
+        const uint32_t pid = tb.out_pid[o0 + i];
+        const uint64_t pos = end_pos + 1 - tb.pat_len[pid];
+        uint4 m = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, text_id);
+        *reinterpret_cast<uint4*>(sk.matches + w) = m;
+    }
+}
+
+// One chain of the walk: a text, the first position read (a multiple of
+// 64), and the owned end positions [start + lo, start + hi).
+struct Chain {
+    const uint32_t* text;
+    uint64_t nwords;
+    uint64_t start;
+    uint32_t lo, hi;  // relative to start
+    uint32_t text_id;
+};
+
+__device__ __forceinline__ void set_chain(Chain& c, const uint32_t* text, uint64_t nwords, uint32_t text_id,
+                                          uint64_t lo, uint64_t hi, uint32_t halo) {
+    c.text = text;
+    c.nwords = nwords;
+    c.text_id = text_id;
+    c.start = (lo > halo ? lo - halo : 0ull) & ~63ull;
+    c.lo = (uint32_t)(lo - c.start);
+    c.hi = (uint32_t)(hi - c.start);
+}
+
+__device__ __forceinline__ void idle_chain(Chain& c, const uint32_t* text, uint64_t nwords, uint32_t text_id) {
+    c.text = text;
+    c.nwords = nwords;
+    c.text_id = text_id;
+    c.start = 0;
+    c.lo = c.hi = 0;
+}
+
+// Threads per block each interleave factor is compiled for (register budget).
+template <int I>
+struct MaxThreads {
+    static constexpr int value = I <= 2 ? 1024 : (I == 4 ? 512 : 256);
+};
+
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int k) {
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// Walk I chains in lockstep (all 32 lanes of the warp call this together).
+template <int I>
+__device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
+                                     const Tables& tb, const Sink& sk, uint64_t pol_tab, uint64_t pol_txt) {
+    uint32_t nb = 0;
+#pragma unroll
+    for (int j = 0; j < I; ++j) {
+        const uint32_t b = (ch[j].hi + 63) >> 6;
+        nb = b > nb ? b : nb;
+    }
+    nb = __reduce_max_sync(FULL, nb);
+    uint32_t s[I];
+#pragma unroll
+    for (int j = 0; j < I; ++j) s[j] = 0;
+
+    for (uint32_t b = 0; b < nb; ++b) {
+        uint4 buf[I];
+        uint32_t fmask[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const bool act = 64u * b < ch[j].hi;
+            fmask[j] = act ? AC_FLAG : 0u;
+            buf[j] = act ? load_block(ch[j].text, (ch[j].start >> 4) + 4ull * b, ch[j].nwords, pol_txt)
+                         : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int wq = 0; wq < 4; ++wq) {
+            uint32_t wd[I];
+#pragma unroll
+            for (int j = 0; j < I; ++j) wd[j] = word_of(buf[j], wq);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                uint32_t e[I];
+#pragma unroll
+                for (int j = 0; j < I; ++j) {
+                    const uint32_t idx = (s[j] << 2) | ((wd[j] >> (2 * q)) & 3u);
+                    e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta + idx, pol_tab);
+                }
+                uint32_t any = 0;
+#pragma unroll
+                for (int j = 0; j < I; ++j) {
+                    s[j] = e[j] & AC_STATE_MASK;
+                    any |= e[j] & fmask[j];
+                }
+                if (__any_sync(FULL, any)) {
+#pragma unroll
+                    for (int j = 0; j < I; ++j) {
+                        const bool f = (e[j] & fmask[j]) != 0;
+                        if (__any_sync(FULL, f)) {
+                            const uint32_t off = 64u * b + 16 * wq + q;
+                            emit_warp(f && off >= ch[j].lo && off < ch[j].hi, s[j], ch[j].start + off,
+                                      ch[j].text_id, tb, sk);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* delta, uint32_t hot) {
+    const uint4* g = reinterpret_cast<const uint4*>(delta);
+    for (uint32_t r = threadIdx.x; r < hot; r += blockDim.x) sm_rows[r] = __ldg(g + r);
+    __syncthreads();
+}
+
+template <int I>
+__global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
+    extern __shared__ uint4 sm_rows[];
+    stage_hot(sm_rows, a.delta, hot);
+    const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
+    const uint64_t pol_tab = policy_evict_last();
+    const uint64_t pol_txt = policy_evict_first();
+    const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nwords = (a.n + 15) >> 4;
+    for (uint64_t round = 0; round < n_chunks; round += T * I) {  // uniform over the grid
+        Chain ch[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const uint64_t c = round + (uint64_t)j * T + t;
+            if (c < n_chunks) {
+                const uint64_t lo = a.own_begin + c * chunk;
+                set_chain(ch[j], a.text, nwords, a.text_id, lo, min(lo + chunk, a.own_end), a.halo);
+            } else {
+                idle_chain(ch[j], a.text, nwords, a.text_id);
+            }
+        }
+        walk<I>(ch, sm, hot, tb, sk, pol_tab, pol_txt);
+    }
+}
+
+// Persistent batched scan: warps take 32*I work items at a time from a
+// device cursor; item -> (text, chunk) by binary search over item_prefix.
+template <int I>
+__global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a, uint32_t hot) {
+    extern __shared__ uint4 sm_rows[];
+    stage_hot(sm_rows, a.delta, hot);
+    const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
+    const uint64_t pol_tab = policy_evict_last();
+    const uint64_t pol_txt = policy_evict_first();
+    const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.counter[1], (unsigned long long)(32 * I));
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= a.n_items) break;
+        Chain ch[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const unsigned long long item = base + (unsigned long long)j * 32 + lane;
+            idle_chain(ch[j], nullptr, 0, 0);
+            if (item < a.n_items) {
+                uint32_t lo_t = 0, hi_t = a.n_texts;  // find t: prefix[t] <= item < prefix[t+1]
+                while (hi_t - lo_t > 1) {
+                    const uint32_t mid = (lo_t + hi_t) >> 1;
+                    if (a.item_prefix[mid] <= item) lo_t = mid; else hi_t = mid;
+                }
+                const BatchText bt = a.texts[lo_t];
+                const uint64_t lo = (item - a.item_prefix[lo_t]) * (uint64_t)a.chunk;
+                set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
+            }
+        }
+        walk<I>(ch, sm, hot, tb, sk, pol_tab, pol_txt);
+    }
+}
+
+__global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint32_t* __restrict__ packed, int fold,
+                            unsigned long long* bad) {
+    const uint64_t nw = (n + 15) >> 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += stride) {
+        const uint64_t b0 = w << 4;
+        uint32_t by[4];
+        if (b0 + 16 <= n && ((reinterpret_cast<uintptr_t>(ascii + b0) & 15) == 0)) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(ascii + b0));
+            by[0] = v.x; by[1] = v.y; by[2] = v.z; by[3] = v.w;
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                uint32_t x = 0;
+                for (int i = 0; i < 4; ++i) {
+                    const uint64_t o = b0 + 4 * k + i;
+                    x |= (uint32_t)(o < n ? ascii[o] : 'A') << (8 * i);
+                }
+                by[k] = x;
+            }
+        }
+        uint32_t word = 0;
+        uint64_t first_bad = ~0ull;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            uint32_t c = (by[i >> 2] >> (8 * (i & 3))) & 0xffu;
+            const uint32_t u = fold ? (c & 0xdfu) : c;
+            const bool ok = (u == 'A') | (u == 'C') | (u == 'G') | (u == 'T');
+            if (!ok && b0 + i < n && first_bad == ~0ull) first_bad = b0 + i;
+            word |= (((c >> 1) ^ (c >> 2)) & 3u) << (2 * i);  // A,C,G,T (either case) -> 0,1,2,3
+        }
+        packed[w] = word;
+        if (first_bad != ~0ull) atomicMin(bad, (unsigned long long)first_bad);
+    }
+}
+
+// counts[p] = sum over states s with p in output(s) of hits[s]
+__global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint32_t* __restrict__ out_pid,
+                              uint32_t n_states, const unsigned long long* __restrict__ hits,
+                              unsigned long long* counts) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_states; s += stride) {
+        const unsigned long long h = hits[s];
+        if (!h) continue;
+        for (uint32_t k = out_off[s]; k < out_off[s + 1]; ++k) atomicAdd(&counts[out_pid[k]], h);
+    }
+}
+
+template <typename K>
+int set_smem(K kern, size_t bytes) {
+    return (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+const DeviceProps& ac_device_props() {
+    static thread_local DeviceProps cache[64];
+    static thread_local bool have[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!have[dev]) {
+        DeviceProps p;
+        p.device = dev;
+        cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        p.smem_optin = (size_t)v;
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+        p.l2 = (size_t)v;
+        cache[dev] = p;
+        have[dev] = true;
+    }
+    return cache[dev];
+}
+
+uint32_t ac_max_threads(uint32_t interleave) {
+    switch (interleave) {
+        case 1: return MaxThreads<1>::value;
+        case 2: return MaxThreads<2>::value;
+        case 4: return MaxThreads<4>::value;
+        case 8: return MaxThreads<8>::value;
+        default: return 0;
+    }
+}
+
+uint32_t ac_max_hot_states() {
+    const DeviceProps& p = ac_device_props();
+    return (uint32_t)(p.smem_optin / 16);
+}
+
+namespace {
+template <int I>
+uint32_t occupancy_for(const ScanShape& sh) {
+    const size_t smem = (size_t)sh.hot * 16;
+    if (set_smem(scan_kernel<I>, smem) != 0) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I>, (int)sh.threads, smem) != cudaSuccess)
+        return 0;
+    return (uint32_t)nb;
+}
+}  // namespace
+
+uint32_t ac_blocks_per_sm(const ScanShape& sh) {
+    switch (sh.interleave) {
+        case 1: return occupancy_for<1>(sh);
+        case 2: return occupancy_for<2>(sh);
+        case 4: return occupancy_for<4>(sh);
+        case 8: return occupancy_for<8>(sh);
+        default: return 0;
+    }
+}
+
+int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold, unsigned long long* bad,
+                   void* stream) {
+    if (n == 0) return 0;
+    const uint64_t nw = (n + 15) >> 4;
+    const DeviceProps& p = ac_device_props();
+    uint64_t blocks = (nw + 255) / 256;
+    const uint64_t cap = (uint64_t)p.sms * 8;
+    if (blocks > cap) blocks = cap;
+    pack_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ascii, n, packed, fold ? 1 : 0, bad);
+    return (int)cudaGetLastError();
+}
+
+int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
+    const uint64_t owned = a.own_end > a.own_begin ? a.own_end - a.own_begin : 0;
+    if (owned == 0) return 0;
+    const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
+    const size_t smem = (size_t)sh.hot * 16;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = 0;
+#define LAUNCH(II)                                                                       \
+    case II:                                                                             \
+        rc = set_smem(scan_kernel<II>, smem);                                            \
+        if (rc) return rc;                                                               \
+        scan_kernel<II><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks); \
+        break;
+    switch (sh.interleave) {
+        LAUNCH(1)
+        LAUNCH(2)
+        LAUNCH(4)
+        LAUNCH(8)
+        default: return (int)cudaErrorInvalidValue;
+    }
+#undef LAUNCH
+    return (int)cudaGetLastError();
+}
+
+int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
+    if (a.n_items == 0) return 0;
+    const size_t smem = (size_t)sh.hot * 16;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = 0;
+#define LAUNCH(II)                                                               \
+    case II:                                                                     \
+        rc = set_smem(batch_kernel<II>, smem);                                   \
+        if (rc) return rc;                                                       \
+        batch_kernel<II><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);          \
+        break;
+    switch (sh.interleave) {
+        LAUNCH(1)
+        LAUNCH(2)
+        LAUNCH(4)
+        LAUNCH(8)
+        default: return (int)cudaErrorInvalidValue;
+    }
+#undef LAUNCH
+    return (int)cudaGetLastError();
+}
+
+int ac_prepare_batch(const ScanShape& sh) {
+    const size_t smem = (size_t)sh.hot * 16;
+    switch (sh.interleave) {
+        case 1: return set_smem(batch_kernel<1>, smem);
+        case 2: return set_smem(batch_kernel<2>, smem);
+        case 4: return set_smem(batch_kernel<4>, smem);
+        case 8: return set_smem(batch_kernel<8>, smem);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,
+                     const unsigned long long* hits, unsigned long long* counts, void* stream) {
+    if (n_states == 0) return 0;
+    const DeviceProps& p = ac_device_props();
+    uint32_t blocks = (n_states + 255) / 256;
+    const uint32_t cap = (uint32_t)p.sms * 8;
+    if (blocks > cap) blocks = cap;
+    counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_pid, n_states, hits, counts);
+    return (int)cudaGetLastError();
+}

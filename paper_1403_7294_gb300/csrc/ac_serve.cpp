@@ -1,0 +1,462 @@
+// ac_serve.cpp - continuous batching of scan requests over resident dfas.
+//
+// Requests arrive with ac_serve_submit (host texts, copied at submit) and
+// wait in one queue. n_streams worker threads each own a CUDA stream. A free
+// worker takes the oldest waiting request, adds younger requests for the same
+// dfa (oldest first) up to max_batch, as long as the device bytes of the
+// work in flight on all workers stay within the budget (memory admission),
+// and runs them as one batched scan on its stream. While it runs, other
+// workers form and launch further batches from requests that arrived in the
+// meantime, so scans of different sizes overlap on the device.
+//
+// A request's device bytes: its packed text (n/4), its ASCII text if it came
+// as ASCII (n), and its output reservation (16 B per reserved occurrence).
+// Per-request results are exactly the stand-alone scan's: the batch writes
+// every occurrence with its text index, the worker splits them per request,
+// and per-keyword counts are the histogram of each request's occurrences. If
+// a batch overflows its reservation, every request of that batch is re-run
+// alone with an exactly sized buffer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ac_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    uint32_t slot = 0;
+    int32_t encoding = AC_TEXT_ASCII;
+    uint64_t n = 0;
+    std::vector<uint8_t> bytes;  // ASCII bytes or packed words
+    uint64_t reserve = 0;        // occurrences reserved
+    uint64_t dev_bytes = 0;
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+    int status = AC_OK;
+    std::vector<ac_match> matches;
+    std::vector<uint64_t> counts;
+    uint64_t n_matches = 0;
+};
+
+uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
+
+struct PinnedBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes) {
+        if (bytes <= cap) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)1 << 24);
+        if (cudaMallocHost(&p, want) != cudaSuccess) return false;
+        cap = want;
+        return true;
+    }
+    ~PinnedBuf() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+}  // namespace
+
+struct ac_server {
+    ac_serve_opts opts{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work;  // workers: new requests / freed budget / stop
+    std::condition_variable cv_done;  // waiters: completions
+    std::vector<const ac_dfa*> dfas;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> by_ticket;
+    uint64_t next_ticket = 1;
+    uint64_t in_flight_bytes = 0;
+    uint32_t in_flight_reqs = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    // stats
+    uint64_t submitted = 0, completed = 0, rejected = 0, failed = 0, bases_completed = 0, batches = 0;
+    std::vector<double> lat_ms;
+    double busy_s = 0.0;
+    Clock::time_point busy_since;
+    uint32_t active_batches = 0;
+
+    void worker_main(int idx);
+    void run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>& batch, PinnedBuf& stage,
+                   PinnedBuf& results);
+};
+
+namespace {
+
+// Stand-alone scan of one request (overflow fallback): exact capacity.
+int scan_alone(const ac_dfa* dfa, Request& r, cudaStream_t st) {
+    ac_text t{r.bytes.data(), r.n, r.encoding, 0};
+    ac_result res;
+    std::memset(&res, 0, sizeof res);
+    res.counts = nullptr;
+    res.on_device = 0;
+    int s = ac_scan(dfa, &t, &res, nullptr, st, nullptr);  // counts the occurrences
+    if (s != AC_OK && s != AC_ERR_OVERFLOW) return s;
+    r.matches.resize(res.n_matches);
+    r.counts.assign(dfa->host.n_patterns, 0);
+    res.matches = r.matches.data();
+    res.capacity = res.n_matches;
+    res.counts = r.counts.data();
+    s = ac_scan(dfa, &t, &res, nullptr, st, nullptr);
+    r.n_matches = res.n_matches;
+    return s;
+}
+
+}  // namespace
+
+void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>& batch, PinnedBuf& stage,
+                          PinnedBuf& results) {
+    const ac_dfa* dfa = dfas[batch[0]->slot];
+    const uint32_t P = dfa->host.n_patterns;
+    // ASCII requests first (one pack over their contiguous slots), packed after
+    std::stable_sort(batch.begin(), batch.end(), [](const std::shared_ptr<Request>& a,
+                                                     const std::shared_ptr<Request>& b) {
+        return a->encoding == AC_TEXT_ASCII && b->encoding != AC_TEXT_ASCII;
+    });
+    const size_t B = batch.size();
+    std::vector<uint64_t> slot(B + 1, 0);  // bases, 64-aligned
+    uint64_t ascii_bases = 0, reserve = 0;
+    for (size_t i = 0; i < B; ++i) {
+        slot[i + 1] = slot[i] + round_up(batch[i]->n, 64);
+        if (batch[i]->encoding == AC_TEXT_ASCII) ascii_bases = slot[i + 1];
+        reserve += batch[i]->reserve;
+    }
+    const uint64_t all = slot[B];
+    const size_t packed_bytes = all / 4;
+    int status = AC_OK;
+    uint8_t* d_ascii = nullptr;
+    uint32_t* d_packed = nullptr;
+    ac_match* d_m = nullptr;
+    auto fail_all = [&](int s) { status = s; };
+
+    // ---- stage: ASCII bytes padded with 'A', then packed words
+    if (!stage.ensure(std::max<size_t>(ascii_bases + packed_bytes, 16))) fail_all(AC_ERR_OOM);
+    if (status == AC_OK) {
+        uint8_t* h_ascii = (uint8_t*)stage.p;
+        uint8_t* h_packed = h_ascii + ascii_bases;
+        for (size_t i = 0; i < B; ++i) {
+            Request& r = *batch[i];
+            if (r.encoding == AC_TEXT_ASCII) {
+                std::memcpy(h_ascii + slot[i], r.bytes.data(), r.n);
+                std::memset(h_ascii + slot[i] + r.n, 'A', slot[i + 1] - slot[i] - r.n);
+            } else {
+                const size_t wb = (r.n + 15) / 16 * 4;
+                std::memcpy(h_packed + slot[i] / 4 - ascii_bases / 4, r.bytes.data(), wb);
+            }
+        }
+        if (cudaMallocAsync((void**)&d_packed, std::max<size_t>(packed_bytes, 16), st) != cudaSuccess ||
+            (ascii_bases && cudaMallocAsync((void**)&d_ascii, ascii_bases, st) != cudaSuccess) ||
+            cudaMallocAsync((void**)&d_m, std::max<uint64_t>(reserve, 1) * sizeof(ac_match), st) != cudaSuccess)
+            fail_all(AC_ERR_OOM);
+    }
+    if (status == AC_OK) {
+        if (ascii_bases) cudaMemcpyAsync(d_ascii, stage.p, ascii_bases, cudaMemcpyHostToDevice, st);
+        if (all > ascii_bases)
+            cudaMemcpyAsync((uint8_t*)d_packed + ascii_bases / 4, (uint8_t*)stage.p + ascii_bases,
+                            (all - ascii_bases) / 4, cudaMemcpyHostToDevice, st);
+        if (ascii_bases) {
+            uint64_t bad = ~0ull;
+            int s = ac_pack(d_ascii, ascii_bases, d_packed, 0, &bad, st);
+            if (s == AC_ERR_ALPHABET) {
+                // find the request that holds the bad byte; fail only that one
+                for (size_t i = 0; i < B; ++i)
+                    if (bad >= slot[i] && bad < slot[i + 1]) batch[i]->status = AC_ERR_ALPHABET;
+            } else if (s != AC_OK) {
+                fail_all(s);
+            }
+        }
+    }
+    // ---- the batched scan
+    uint64_t nm = 0;
+    if (status == AC_OK) {
+        std::vector<ac_text> texts(B);
+        for (size_t i = 0; i < B; ++i) texts[i] = ac_text{d_packed + slot[i] / 16, batch[i]->n, AC_TEXT_PACKED2, 1};
+        ac_result res;
+        std::memset(&res, 0, sizeof res);
+        res.matches = d_m;
+        res.capacity = reserve;
+        res.on_device = 1;
+        int s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
+        nm = res.n_matches;
+        if (s == AC_ERR_OVERFLOW) {
+            for (auto& r : batch)
+                if (r->status == AC_OK) r->status = scan_alone(dfa, *r, st);
+            nm = 0;
+        } else if (s != AC_OK) {
+            fail_all(s);
+        } else {
+            const size_t mb = nm * sizeof(ac_match);
+            if (!results.ensure(std::max<size_t>(mb, 16))) {
+                fail_all(AC_ERR_OOM);
+            } else {
+                if (nm) cudaMemcpyAsync(results.p, d_m, mb, cudaMemcpyDeviceToHost, st);
+                if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
+            }
+            if (status == AC_OK) {
+                // split per request (counting sort by text index)
+                const ac_match* m = (const ac_match*)results.p;
+                std::vector<uint64_t> per(B, 0);
+                for (uint64_t k = 0; k < nm; ++k) per[m[k].text_id]++;
+                for (size_t i = 0; i < B; ++i) {
+                    Request& r = *batch[i];
+                    if (r.status != AC_OK) continue;
+                    r.matches.clear();
+                    r.matches.reserve(per[i]);
+                    r.counts.assign(P, 0);
+                    r.n_matches = per[i];
+                }
+                for (uint64_t k = 0; k < nm; ++k) {
+                    Request& r = *batch[m[k].text_id];
+                    if (r.status != AC_OK) continue;
+                    ac_match x = m[k];
+                    x.text_id = 0;
+                    r.matches.push_back(x);
+                    r.counts[x.pattern_id]++;
+                }
+            }
+        }
+    }
+    if (d_ascii) cudaFreeAsync(d_ascii, st);
+    if (d_packed) cudaFreeAsync(d_packed, st);
+    if (d_m) cudaFreeAsync(d_m, st);
+    cudaStreamSynchronize(st);
+    const auto now = Clock::now();
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& r : batch) {
+        if (status != AC_OK && r->status == AC_OK) r->status = status;
+        r->done = true;
+        r->t_done = now;
+        in_flight_bytes -= r->dev_bytes;
+        in_flight_reqs -= 1;
+        if (r->status == AC_OK) {
+            completed++;
+            bases_completed += r->n;
+            lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+        } else {
+            failed++;
+        }
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+}
+
+void ac_server::worker_main(int idx) {
+    (void)idx;
+    cudaSetDevice(device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    PinnedBuf stage, results;
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> batch;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            for (;;) {
+                if (stop && pending.empty()) {
+                    lk.unlock();
+                    cudaStreamDestroy(st);
+                    return;
+                }
+                if (!pending.empty()) {
+                    const uint32_t slot = pending.front()->slot;
+                    uint64_t bytes = in_flight_bytes;
+                    for (auto it = pending.begin(); it != pending.end() && batch.size() < opts.max_batch;) {
+                        if ((*it)->slot == slot && bytes + (*it)->dev_bytes <= opts.device_budget_bytes) {
+                            bytes += (*it)->dev_bytes;
+                            batch.push_back(*it);
+                            it = pending.erase(it);
+                        } else if (batch.empty()) {
+                            break;  // the oldest waits until the budget frees up
+                        } else {
+                            ++it;
+                        }
+                    }
+                    if (!batch.empty()) {
+                        in_flight_bytes = bytes;
+                        in_flight_reqs += (uint32_t)batch.size();
+                        if (active_batches++ == 0) busy_since = Clock::now();
+                        batches++;
+                        break;
+                    }
+                }
+                cv_work.wait(lk);
+            }
+        }
+        run_batch(st, batch, stage, results);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (--active_batches == 0)
+                busy_s += std::chrono::duration<double>(Clock::now() - busy_since).count();
+        }
+    }
+}
+
+extern "C" int ac_serve_create(const ac_serve_opts* opts, ac_server** out) {
+    if (!out) return AC_ERR_INVALID_ARG;
+    ac_server* s = new (std::nothrow) ac_server();
+    if (!s) return AC_ERR_OOM;
+    if (opts) s->opts = *opts;
+    if (!s->opts.device_budget_bytes) s->opts.device_budget_bytes = 40ull << 30;
+    if (!s->opts.n_streams) s->opts.n_streams = 4;
+    if (!s->opts.max_batch) s->opts.max_batch = 256;
+    if (!s->opts.max_queue) s->opts.max_queue = 1u << 16;
+    if (!s->opts.match_capacity_per_base_x1000) s->opts.match_capacity_per_base_x1000 = 64;
+    cudaGetDevice(&s->device);
+    try {
+        for (uint32_t i = 0; i < s->opts.n_streams; ++i) s->workers.emplace_back(&ac_server::worker_main, s, (int)i);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        for (auto& t : s->workers) t.join();
+        delete s;
+        return AC_ERR_OOM;
+    }
+    *out = s;
+    return AC_OK;
+}
+
+extern "C" int ac_serve_add_dfa(ac_server* s, const ac_dfa* dfa, uint32_t* slot) {
+    if (!s || !dfa || !slot) return AC_ERR_INVALID_ARG;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->dfas.push_back(dfa);
+    *slot = (uint32_t)(s->dfas.size() - 1);
+    return AC_OK;
+}
+
+extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, uint64_t* ticket) {
+    if (!s || !t || !ticket) return AC_ERR_INVALID_ARG;
+    if (t->on_device) return AC_ERR_INVALID_ARG;
+    if (t->encoding != AC_TEXT_ASCII && t->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    if (t->n_bases && !t->data) return AC_ERR_INVALID_ARG;
+    if (t->encoding == AC_TEXT_ASCII) {  // reject bad input before it is queued
+        const uint8_t* b = (const uint8_t*)t->data;
+        for (uint64_t i = 0; i < t->n_bases; ++i)
+            if (b[i] != 'A' && b[i] != 'C' && b[i] != 'G' && b[i] != 'T') return AC_ERR_ALPHABET;
+    }
+    auto r = std::make_shared<Request>();
+    r->slot = slot;
+    r->encoding = t->encoding;
+    r->n = t->n_bases;
+    r->reserve = t->n_bases * s->opts.match_capacity_per_base_x1000 / 1000 + 1024;
+    const uint64_t nb = t->encoding == AC_TEXT_ASCII ? t->n_bases : (t->n_bases + 15) / 16 * 4;
+    r->dev_bytes = round_up(t->n_bases, 64) / 4 + (t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : 0) +
+                   r->reserve * sizeof(ac_match);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (slot >= s->dfas.size()) return AC_ERR_NOT_FOUND;
+        if (s->stop || s->pending.size() >= s->opts.max_queue || r->dev_bytes > s->opts.device_budget_bytes) {
+            s->rejected++;
+            return AC_ERR_BUSY;
+        }
+    }
+    try {
+        r->bytes.assign((const uint8_t*)t->data, (const uint8_t*)t->data + nb);
+    } catch (const std::bad_alloc&) {
+        return AC_ERR_OOM;
+    }
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->ticket = s->next_ticket++;
+        s->by_ticket[r->ticket] = r;
+        s->pending.push_back(r);
+        s->submitted++;
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return AC_OK;
+}
+
+extern "C" int ac_serve_wait(ac_server* s, uint64_t ticket, ac_result* res, int64_t timeout_us) {
+    if (!s || !res) return AC_ERR_INVALID_ARG;
+    if (res->on_device || (res->capacity && !res->matches)) return AC_ERR_INVALID_ARG;
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->by_ticket.find(ticket);
+        if (it == s->by_ticket.end()) return AC_ERR_NOT_FOUND;
+        r = it->second;
+        auto ready = [&] { return r->done; };
+        if (timeout_us < 0) {
+            s->cv_done.wait(lk, ready);
+        } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+            return AC_ERR_TIMEOUT;
+        }
+        res->bad_offset = ~0ull;
+        res->n_matches = r->n_matches;
+        if (r->status == AC_OK && r->n_matches > res->capacity) return AC_ERR_OVERFLOW;  // ticket stays valid
+        s->by_ticket.erase(ticket);
+    }
+    if (r->status != AC_OK) return r->status;
+    if (r->n_matches) std::memcpy(res->matches, r->matches.data(), r->n_matches * sizeof(ac_match));
+    if (res->counts && !r->counts.empty()) std::memcpy(res->counts, r->counts.data(), r->counts.size() * 8);
+    return AC_OK;
+}
+
+extern "C" int ac_serve_stats(ac_server* s, ac_serve_stats_t* o) {
+    if (!s || !o) return AC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(o, 0, sizeof *o);
+    o->submitted = s->submitted;
+    o->completed = s->completed;
+    o->rejected = s->rejected;
+    o->failed = s->failed;
+    o->bases_completed = s->bases_completed;
+    o->batches_launched = s->batches;
+    double busy = s->busy_s;
+    if (s->active_batches) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
+    o->busy_s = busy;
+    o->gbases_per_s = busy > 0 ? (double)s->bases_completed / busy / 1e9 : 0.0;
+    if (!s->lat_ms.empty()) {
+        std::vector<double> v = s->lat_ms;
+        auto pct = [&](double q) {
+            size_t k = (size_t)std::min<double>((double)v.size() - 1, std::max(0.0, q * (double)(v.size() - 1) + 0.5));
+            std::nth_element(v.begin(), v.begin() + k, v.end());
+            return v[k];
+        };
+        o->p50_ms = pct(0.50);
+        o->p99_ms = pct(0.99);
+        double sum = 0, mx = 0;
+        for (double x : s->lat_ms) {
+            sum += x;
+            mx = std::max(mx, x);
+        }
+        o->mean_ms = sum / (double)s->lat_ms.size();
+        o->max_ms = mx;
+    }
+    return AC_OK;
+}
+
+extern "C" void ac_serve_destroy(ac_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
+}

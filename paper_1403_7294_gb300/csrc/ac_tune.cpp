@@ -1,0 +1,191 @@
+// ac_tune.cpp - launch-shape autotuner for the scan kernels.
+//
+// A shape is (threads per block, chunks walked per thread, states staged in
+// shared memory); the chunk length follows from the shape (one wave of
+// resident lanes over the text). ac_autotune times every candidate with CUDA
+// events on a sample text and keeps the fastest per (device, machine size
+// class, text size class), where a size class is ceil(log2(x)). Later scans
+// whose classes match use the tuned shape unless the caller fixes one.
+//
+// Environment:
+//   AC_TUNE=off          skip the trials; return the built-in default shape
+//   AC_TUNE_CACHE=path   load tuned shapes from / append them to a JSON file
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ac_internal.h"
+
+namespace {
+
+using Key = std::tuple<std::string, uint32_t, uint32_t>;  // device name+sms, log2 S, log2 n
+
+struct Entry {
+    uint32_t threads, interleave, hot;
+    float ms;
+};
+
+std::mutex g_mu;
+std::map<Key, Entry> g_cache;
+bool g_loaded = false;
+
+uint32_t size_class(uint64_t x) { return x <= 1 ? 0u : (uint32_t)std::ceil(std::log2((double)x)); }
+
+std::string device_tag() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    std::string s = p.name;
+    for (char& c : s)
+        if (c == ' ' || c == '"') c = '_';
+    return s + "_sm" + std::to_string(p.multiProcessorCount);
+}
+
+// Cache file: one JSON object per line:
+// {"device": "...", "s_class": N, "n_class": N, "threads": N, "interleave": N, "hot": N, "ms": F}
+void load_file_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char* path = std::getenv("AC_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512], dev[256];
+    while (std::fgets(line, sizeof line, f)) {
+        unsigned sc, nc, th, il, hot;
+        float ms;
+        if (std::sscanf(line,
+                        " {\"device\": \"%255[^\"]\", \"s_class\": %u, \"n_class\": %u, \"threads\": %u, "
+                        "\"interleave\": %u, \"hot\": %u, \"ms\": %f}",
+                        dev, &sc, &nc, &th, &il, &hot, &ms) == 7)
+            g_cache[Key{dev, sc, nc}] = Entry{th, il, hot, ms};
+    }
+    std::fclose(f);
+}
+
+void append_file(const Key& k, const Entry& e) {
+    const char* path = std::getenv("AC_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"device\": \"%s\", \"s_class\": %u, \"n_class\": %u, \"threads\": %u, \"interleave\": %u, "
+                 "\"hot\": %u, \"ms\": %.6f}\n",
+                 std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), e.threads, e.interleave, e.hot, e.ms);
+    std::fclose(f);
+}
+
+bool tuning_off() {
+    const char* v = std::getenv("AC_TUNE");
+    return v && (std::strcmp(v, "off") == 0 || std::strcmp(v, "0") == 0);
+}
+
+}  // namespace
+
+bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_file_locked();
+    if (g_cache.empty()) return false;
+    auto it = g_cache.find(Key{device_tag(), size_class(dfa->host.n_states), size_class(n)});
+    if (it == g_cache.end()) return false;
+    out->threads = it->second.threads;
+    out->interleave = it->second.interleave;
+    out->hot = it->second.hot;
+    out->chunk = 0;
+    return true;
+}
+
+extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opts* best, void* stream) {
+    if (!dfa || !sample || !best) return AC_ERR_INVALID_ARG;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    if (!sample->on_device || sample->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    const uint64_t n = sample->n_bases;
+    std::memset(best, 0, sizeof *best);
+    best->hot_states = -1;
+    const Key key{device_tag(), size_class(dfa->host.n_states), size_class(n)};
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_file_locked();
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            best->threads = it->second.threads;
+            best->interleave = it->second.interleave;
+            best->hot_states = (int32_t)it->second.hot;
+            return AC_OK;
+        }
+    }
+    const uint32_t S = dfa->host.n_states;
+    const uint32_t max_hot = std::min(S, ac_max_hot_states());
+    if (tuning_off() || n == 0) {
+        best->interleave = 4;
+        best->threads = ac_max_threads(4);
+        best->hot_states = (int32_t)max_hot;
+        return AC_OK;
+    }
+    // a scratch occurrence buffer so emission costs what it costs in real use
+    const uint64_t cap = std::min<uint64_t>(1u << 22, n / 8 + 1024);
+    ac_match* d_m = nullptr;
+    if (cudaMalloc(&d_m, cap * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
+
+    std::vector<uint32_t> hots = {max_hot};
+    if (max_hot > 1024) hots.push_back(max_hot / 2);
+    if (max_hot > 2048) hots.push_back(max_hot / 4);
+    const uint32_t threads_c[] = {256, 512, 1024};
+    const uint32_t inter_c[] = {1, 2, 4, 8};
+    Entry top{0, 0, 0, 1e30f};
+    int rc = AC_OK;
+    for (uint32_t hot : hots)
+        for (uint32_t th : threads_c)
+            for (uint32_t il : inter_c) {
+                if (th > ac_max_threads(il)) continue;
+                ac_scan_opts o;
+                std::memset(&o, 0, sizeof o);
+                o.threads = th;
+                o.interleave = il;
+                o.hot_states = (int32_t)hot;
+                ScanShape probe;
+                probe.threads = th;
+                probe.interleave = il;
+                probe.hot = hot;
+                if (ac_blocks_per_sm(probe) == 0) continue;  // does not fit
+                float t_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    ac_result r;
+                    std::memset(&r, 0, sizeof r);
+                    r.matches = d_m;
+                    r.capacity = cap;
+                    r.on_device = 1;
+                    ac_scan_stats stt;
+                    int s = ac_scan(dfa, sample, &r, &o, stream, &stt);
+                    if (s != AC_OK && s != AC_ERR_OVERFLOW) {
+                        rc = s;
+                        break;
+                    }
+                    if (rep > 0) t_best = std::min(t_best, stt.scan_ms);
+                }
+                if (rc != AC_OK) break;
+                if (t_best < top.ms) top = Entry{th, il, hot, t_best};
+            }
+    cudaFree(d_m);
+    if (rc != AC_OK) return rc;
+    if (top.threads == 0) return AC_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_cache[key] = top;
+        append_file(key, top);
+    }
+    best->threads = top.threads;
+    best->interleave = top.interleave;
+    best->hot_states = (int32_t)top.hot;
+    return AC_OK;
+}

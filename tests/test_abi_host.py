@@ -1,0 +1,187 @@
+"""CPU tests of the C-ABI library: it loads, exports and binds every function
+that include/ac.h declares, validates its inputs, and its host builder (stage 1
+of Sec. III.A, flattened) agrees with the oracle. No GPU is used: dfas are
+built with AC_BUILD_HOST_ONLY and their tables are walked in Python."""
+import os
+import random
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1403_7294_gb300 as acg
+from paper_1403_7294_gb300 import _native as N
+from tests.conftest import ROOT, load_golden
+
+HEADER = os.path.join(ROOT, "include", "ac.h")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(ac_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    fns = header_functions()
+    for name in ("ac_build", "ac_scan", "ac_scan_batch", "ac_serve_create", "ac_serve_submit", "ac_serve_wait"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_function():
+    lib = acg.lib()
+    nm = subprocess.run(["nm", "-D", "--defined-only", N.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (ac_\w+)$", nm, flags=re.M))
+    for name in header_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_binding_covers_every_declared_function():
+    assert sorted(N.SIGNATURES) == header_functions()
+
+
+def test_status_strings():
+    lib = acg.lib()
+    for code in range(0, -12, -1):
+        assert lib.ac_status_str(code).decode() != "unknown status"
+    assert lib.ac_status_str(-99).decode() == "unknown status"
+
+
+def test_struct_sizes_match_the_header():
+    import ctypes
+
+    assert ctypes.sizeof(N.Match) == 16
+    assert ctypes.sizeof(N.Text) == 24
+    assert ctypes.sizeof(N.Result) == 48
+    assert ctypes.sizeof(N.ScanOpts) == 40
+
+
+# ------------------------------------------------------------ validation
+
+
+@pytest.mark.parametrize(
+    "pats,code",
+    [
+        ([b"ACGT", b""], N.AC_ERR_EMPTY_PATTERN),
+        ([b"ACGN"], N.AC_ERR_ALPHABET),
+        ([b"acgt"], N.AC_ERR_ALPHABET),
+        ([], N.AC_ERR_INVALID_ARG),
+    ],
+)
+def test_build_rejects(pats, code):
+    with pytest.raises(acg.AcError) as e:
+        acg.build(pats, host_only=True)
+    assert e.value.status == code
+
+
+def test_fold_case_accepts_lower_case():
+    d = acg.build([b"acgT"], fold_case=True, host_only=True)
+    assert d.n_states == 5
+
+
+def test_host_only_dfa_cannot_scan():
+    import ctypes
+
+    d = acg.build([b"ACGT"], host_only=True)
+    t = N.Text(None, 0, N.AC_TEXT_ASCII, 0)
+    r = N.Result()
+    st = acg.lib().ac_scan(d.h, ctypes.byref(t), ctypes.byref(r), None, None, None)
+    assert st == N.AC_ERR_NO_DEVICE
+
+
+# ------------------------------------------- builder vs the oracle (CPU)
+
+CODE = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3}
+
+
+def walk_tables(t, text: bytes):
+    """One lookup per base over the flattened table; emits (start, pid)."""
+    delta, off, pid, plen = t["delta"], t["out_off"], t["out_pid"], t["pat_len"]
+    s, out = 0, set()
+    for i, ch in enumerate(text):
+        e = int(delta[4 * s + CODE[ch]])
+        s = e & 0x7FFFFFFF
+        if e >> 31:
+            for k in range(off[s], off[s + 1]):
+                p = int(pid[k])
+                out.add((i + 1 - int(plen[p]), p))
+        else:
+            assert off[s] == off[s + 1], "flag bit clear on a state with output"
+    return out
+
+
+def strings_by_state(t):
+    """string(s) for each breadth-first state, from the depth-increasing tree edges."""
+    delta, depth = t["delta"].reshape(-1, 4), t["depth"]
+    S = len(depth)
+    s_of = {0: b""}
+    for s in range(S):  # breadth-first ids: parents come first
+        for c in range(4):
+            nx = int(delta[s, c]) & 0x7FFFFFFF
+            if depth[nx] == depth[s] + 1 and nx not in s_of:
+                s_of[nx] = s_of[s] + b"ACGT"[c : c + 1]
+    assert len(s_of) == S
+    return s_of
+
+
+def rand_set(rng, k, lo, hi):
+    return [bytes(rng.choice(b"ACGT") for _ in range(rng.randint(lo, hi))) for _ in range(k)]
+
+
+def test_worked_example_dna_tables():
+    g = load_golden("worked_example_dna.txt")
+    kws = [w.encode() for w in g["keywords"][0]]
+    t = acg.build(kws, host_only=True).tables()
+    got = walk_tables(t, g["text"][0][0].encode())
+    assert got == {(int(p), [w.decode() for w in kws].index(k)) for p, k in g["match"]}
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_flattened_walk_equals_oracle(seed):
+    rng = random.Random(500 + seed)
+    pats = rand_set(rng, rng.randint(1, 60), 1, 9)
+    if seed % 4 == 0:
+        pats += [pats[0], pats[-1][:2] or b"A"]  # duplicates and prefixes
+    n = rng.choice([0, 1, 50, 700, 3000])
+    if seed % 5 == 0:
+        text = (b"AC" * n)[:n]
+    else:
+        text = bytes(rng.choice(b"ACGT") for _ in range(n))
+    d = acg.build(pats, host_only=True)
+    t = d.tables()
+    pos, pid, counts = oracle.Machine(pats).scan(text)
+    assert walk_tables(t, text) == set(zip(pos.tolist(), pid.tolist()))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_builder_fail_output_depth_match_oracle(seed):
+    rng = random.Random(900 + seed)
+    pats = rand_set(rng, rng.randint(1, 40), 1, 7)
+    t = acg.build(pats, host_only=True).tables()
+    m = oracle.Machine(pats)
+    strings = strings_by_state(t)
+    # the oracle's state for each string (walk its goto from the root)
+    def orc_state(w):
+        s = 0
+        for c in w:
+            s = m.goto(s, c)
+        return s
+    by_orc = {orc_state(w): s for s, w in strings.items()}
+    assert len(by_orc) == m.n_states == len(strings)
+    for s, w in strings.items():
+        o = orc_state(w)
+        assert t["depth"][s] == m.depth(o) == len(w)
+        assert by_orc[m.fail(o)] == t["fail"][s]
+        assert sorted(t["out_pid"][t["out_off"][s] : t["out_off"][s + 1]].tolist()) == sorted(m.output(o))
+    for p, w in enumerate(pats):
+        assert strings[int(t["pat_state"][p])] == w
+        assert t["pat_len"][p] == len(w)
+
+
+def test_breadth_first_numbering():
+    rng = random.Random(3)
+    t = acg.build(rand_set(rng, 200, 5, 12), host_only=True).tables()
+    assert np.all(np.diff(t["depth"].astype(np.int64)) >= 0)  # depth non-decreasing in id order

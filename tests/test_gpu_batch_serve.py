@@ -1,0 +1,204 @@
+"""GPU parity of the batched scan (ac_scan_batch, batch plans) and of serving.
+
+Batch = the concatenation of per-text scans = the oracle on every text.
+Serving: every request's result is the same alone and in a concurrent mix,
+and equals the oracle (tolerance 0: all results are exact integers)."""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1403_7294_gb300 as acg
+from paper_1403_7294_gb300 import _native as N
+from tests.gpu_helpers import oracle_canonical
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def rand_dna(rng, n):
+    return bytes(rng.choice(b"ACGT") for _ in range(n))
+
+
+def batch_case(seed, n_texts=150):
+    rng = random.Random(seed)
+    lens = [rng.choice([0, 1, 5, 63, 64, 65, 300, 2000, 9000]) for _ in range(n_texts)]
+    texts = [rand_dna(rng, n) for n in lens]
+    src = b"".join(texts)
+    pats = [rand_dna(rng, rng.randint(4, 14)) for _ in range(200)]
+    pats += [src[j : j + rng.randint(4, 14)] for j in rng.sample(range(max(1, len(src) - 20)), 200)]
+    return texts, pats
+
+
+def oracle_batch(pats, texts):
+    rows, counts = [], np.zeros(len(pats), np.int64)
+    for i, t in enumerate(texts):
+        a, c = oracle_canonical(pats, t, text_id=i)
+        rows.append(a)
+        counts += c
+    a = np.concatenate(rows) if rows else np.zeros((0, 3), np.int64)
+    return a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))], counts
+
+
+def packed_dev(texts):
+    out = []
+    for t in texts:
+        if t:
+            out.append(acg.pack(torch.tensor(list(t), dtype=torch.uint8, device=DEV)))
+        else:
+            out.append(torch.zeros(4, dtype=torch.int32, device=DEV))
+    return out
+
+
+@pytest.mark.parametrize("form", ["packed_dev", "ascii_dev", "ascii_host", "packed_host"])
+@pytest.mark.parametrize("interleave", [1, 4])
+def test_batch_vs_oracle(form, interleave):
+    texts, pats = batch_case(11)
+    d = acg.build(pats)
+    want, counts = oracle_batch(pats, texts)
+    lens = [len(t) for t in texts]
+    if form == "packed_dev":
+        arg, enc = packed_dev(texts), N.AC_TEXT_PACKED2
+    elif form == "packed_host":
+        arg, enc = [p.cpu().numpy() for p in packed_dev(texts)], N.AC_TEXT_PACKED2
+    elif form == "ascii_dev":
+        arg = [torch.tensor(list(t), dtype=torch.uint8, device=DEV) if t else torch.empty(0, dtype=torch.uint8, device=DEV)
+               for t in texts]
+        enc = N.AC_TEXT_ASCII
+    else:
+        arg, enc = [np.frombuffer(t, np.uint8) if t else np.zeros(0, np.uint8) for t in texts], N.AC_TEXT_ASCII
+    r = acg.scan_batch(d, arg, encoding=enc, n_bases=lens, capacity=16, interleave=interleave)
+    got = r.canonical()
+    assert np.array_equal(got, want)
+    assert r.counts.cpu().numpy().tolist() == counts.tolist()
+
+
+def test_batch_equals_per_text_loop():
+    texts, pats = batch_case(12, 60)
+    d = acg.build(pats)
+    pk = packed_dev(texts)
+    lens = [len(t) for t in texts]
+    b = acg.scan_batch(d, pk, encoding=N.AC_TEXT_PACKED2, n_bases=lens).canonical()
+    loop = []
+    for i, (p, n) in enumerate(zip(pk, lens)):
+        loop.append(acg.scan(d, p, encoding=N.AC_TEXT_PACKED2, n_bases=n, text_id=i).canonical())
+    loop = np.concatenate(loop)
+    loop = loop[np.lexsort((loop[:, 2], loop[:, 1], loop[:, 0]))]
+    assert np.array_equal(b, loop)
+
+
+@pytest.mark.parametrize("chunk", [0, 64, 1000])
+def test_batch_plan_replays_exactly(chunk):
+    texts, pats = batch_case(13, 100)
+    d = acg.build(pats)
+    want, counts = oracle_batch(pats, texts)
+    pk = packed_dev(texts)
+    plan = acg.BatchPlan(d, pk, [len(t) for t in texts], capacity=len(want) + 10, chunk=chunk)
+    for _ in range(3):  # replays reset their counters
+        assert plan.run() == len(want)
+        assert np.array_equal(plan.result().canonical(), want)
+        assert plan.counts.cpu().numpy().tolist() == counts.tolist()
+    plan.close()
+
+
+def test_batch_plan_overflow_flag():
+    texts = [b"A" * 1000, b"A" * 10]
+    d = acg.build([b"A", b"AA"])
+    plan = acg.BatchPlan(d, packed_dev(texts), [1000, 10], capacity=100)
+    assert plan.run() == 1000 + 999 + 10 + 9 and plan.overflow
+    assert plan.counts.cpu().tolist() == [1010, 1008]
+
+
+# ------------------------------------------------------------------ serving
+
+
+def test_serve_alone_equals_mix_equals_oracle():
+    rng = random.Random(21)
+    genome = rand_dna(rng, 400_000)
+    sets = []
+    for k in range(3):
+        pats = [genome[j : j + rng.randint(10, 20)] for j in rng.sample(range(399_000), 100 + 200 * k)]
+        pats += [rand_dna(rng, 12) for _ in range(50)]
+        sets.append(pats)
+    dfas = [acg.build(p) for p in sets]
+    reqs = []
+    for _ in range(60):
+        n = int(np.exp(rng.uniform(np.log(100), np.log(150_000))))
+        off = rng.randint(0, len(genome) - n)
+        reqs.append((rng.randint(0, 2), genome[off : off + n]))
+    # alone: one request at a time
+    srv = acg.Server(device_budget_bytes=1 << 30, n_streams=3, max_batch=16)
+    slots = [srv.add_dfa(d) for d in dfas]
+    alone = []
+    for s, t in reqs:
+        tk = srv.submit(slots[s], t)
+        alone.append(srv.wait(tk, slots[s], capacity=8))
+    # mix: submitted from 4 threads at once, waited in reverse order
+    tickets = [None] * len(reqs)
+
+    def submitter(idx):
+        for i in idx:
+            s, t = reqs[i]
+            tickets[i] = srv.submit(slots[s], t)
+
+    ths = [threading.Thread(target=submitter, args=(list(range(k, len(reqs), 4)),)) for k in range(4)]
+    [t.start() for t in ths]
+    [t.join() for t in ths]
+    mix = [None] * len(reqs)
+    for i in reversed(range(len(reqs))):
+        mix[i] = srv.wait(tickets[i], slots[reqs[i][0]], capacity=1 << 12)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 2 * len(reqs) and st["failed"] == 0
+    assert st["batches_launched"] < 2 * len(reqs)  # requests were batched together
+    for i, (s, t) in enumerate(reqs):
+        a = alone[i][0][np.lexsort((alone[i][0][:, 1], alone[i][0][:, 0]))]
+        m = mix[i][0][np.lexsort((mix[i][0][:, 1], mix[i][0][:, 0]))]
+        assert np.array_equal(a, m)
+        assert np.array_equal(alone[i][1], mix[i][1])
+        want, counts = oracle_canonical(sets[s], t)
+        assert np.array_equal(a, want[:, 1:])
+        assert np.array_equal(alone[i][1], counts)
+
+
+def test_serve_admission_and_errors():
+    d = acg.build([b"ACGT"])
+    srv = acg.Server(device_budget_bytes=1 << 20, n_streams=1, max_batch=4, max_queue=2)
+    slot = srv.add_dfa(d)
+    big = b"A" * (1 << 20)  # alone exceeds the device budget
+    assert srv.try_submit(slot, big) is None
+    with pytest.raises(acg.AcError) as e:
+        srv.submit(slot, b"ACGN")
+    assert e.value.status == N.AC_ERR_ALPHABET
+    with pytest.raises(acg.AcError) as e:
+        srv.submit(99, b"ACGT")
+    assert e.value.status == N.AC_ERR_NOT_FOUND
+    tk = srv.submit(slot, b"ACGTACGT")
+    m, c, k = srv.wait(tk, slot)
+    assert k == 2 and c.tolist() == [2]
+    st = srv.stats()
+    assert st["rejected"] == 1
+    srv.close()
+
+
+def test_serve_wait_timeout_keeps_ticket():
+    d = acg.build([b"ACGT"])
+    srv = acg.Server(n_streams=1)
+    slot = srv.add_dfa(d)
+    tk = srv.submit(slot, b"ACGT" * 1000)
+    import ctypes
+
+    r = N.Result(None, 0, 0, None, 0, 0, 0)
+    t0 = time.time()
+    while True:
+        st = acg.lib().ac_serve_wait(srv.h, tk, ctypes.byref(r), 0)
+        if st != N.AC_ERR_TIMEOUT:
+            break
+        assert time.time() - t0 < 30
+    assert st == N.AC_ERR_OVERFLOW and r.n_matches == 1000  # capacity 0: count reported, ticket kept
+    m, c, k = srv.wait(tk, slot, capacity=1000)
+    assert k == 1000
+    srv.close()

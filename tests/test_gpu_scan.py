@@ -1,0 +1,202 @@
+"""GPU parity of the single-text scan (ac_scan, ac_pack) against the oracle.
+
+Bit-exact comparison after the canonical sort (the occurrence set is unique,
+only its order is free), plus exact per-keyword counts. Covers the worked
+example, seeded fuzz over every launch shape the kernels offer (chunk sizes
+1, 2, L_max-1, L_max, 97, 4096, n; shared-memory states 0, 1, all; interleave
+1, 2, 4, 8), owned ranges, host and device buffers, overflow, alphabet
+errors and the 1 Mbase uniform workload in full."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1403_7294_gb300 as acg
+from paper_1403_7294_gb300 import _native as N
+from paper_1403_7294_gb300 import synth
+from tests.conftest import load_golden
+from tests.gpu_helpers import assert_same, oracle_canonical, unpack_codes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def rand_dna(rng, n):
+    return bytes(rng.choice(b"ACGT") for _ in range(n))
+
+
+def to_dev(b: bytes) -> torch.Tensor:
+    return torch.tensor(list(b), dtype=torch.uint8, device=DEV) if b else torch.empty(0, dtype=torch.uint8, device=DEV)
+
+
+def test_pack_round_trip_and_alphabet():
+    rng = random.Random(1)
+    for n in (1, 15, 16, 17, 63, 64, 65, 1000, 4097):
+        txt = rand_dna(rng, n)
+        packed = acg.pack(to_dev(txt))
+        codes = unpack_codes(packed, n).cpu().numpy()
+        assert codes.tolist() == [b"ACGT".index(c) for c in txt]
+    low = to_dev(b"acgtACGT")
+    assert unpack_codes(acg.pack(low, fold_case=True), 8).tolist() == [0, 1, 2, 3, 0, 1, 2, 3]
+    with pytest.raises(acg.AcError) as e:
+        acg.pack(to_dev(b"ACGTNACGT"))
+    assert e.value.status == N.AC_ERR_ALPHABET and "offset 4" in str(e.value)
+
+
+def test_worked_example_dna():
+    g = load_golden("worked_example_dna.txt")
+    kws = [w.encode() for w in g["keywords"][0]]
+    text = g["text"][0][0].encode()
+    d = acg.build(kws)
+    want = sorted((int(p), [w.decode() for w in kws].index(k)) for p, k in g["match"])
+    for t in (to_dev(text), text):  # device and host ASCII
+        r = acg.scan(d, t)
+        assert sorted(zip(r.pos.tolist(), r.pattern_id.tolist())) == want
+
+
+def _cases(seed, k):
+    rng = random.Random(seed)
+    for _ in range(k):
+        n = rng.choice([0, 1, 31, 64, 65, 200, 1000, 5000, 20000])
+        if rng.random() < 0.25:
+            unit = rand_dna(rng, rng.randint(1, 4))
+            text = (unit * (n // len(unit) + 1))[:n]
+        else:
+            text = rand_dna(rng, n)
+        pats = [rand_dna(rng, rng.randint(1, 12)) for _ in range(rng.randint(1, 40))]
+        if n > 20:
+            for _ in range(rng.randint(0, 10)):
+                j = rng.randint(0, n - 1)
+                p = text[j : j + rng.randint(1, 15)]
+                if p:
+                    pats.append(p)
+        if rng.random() < 0.3:
+            pats.append(pats[0])  # duplicate keyword
+        yield pats, text
+
+
+@pytest.mark.parametrize("shape", ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8"])
+def test_fuzz_vs_oracle(shape):
+    for pats, text in _cases(77, 25):
+        lmax = max(len(p) for p in pats)
+        kw = {}
+        if shape.startswith("c"):
+            kw["chunk"] = {"c1": 1, "c2": 2, "cLm1": max(1, lmax - 1), "cL": lmax, "c97": 97, "c4096": 4096,
+                           "cn": max(1, len(text))}[shape]
+        elif shape == "hot0":
+            kw["hot_states"] = 0
+        elif shape == "hot1":
+            kw["hot_states"] = 1
+        elif shape.startswith("i"):
+            kw["interleave"] = int(shape[1:])
+        d = acg.build(pats)
+        want, counts = oracle_canonical(pats, text)
+        r = acg.scan(d, to_dev(text), capacity=4, **kw)  # tiny capacity: exercises the overflow retry
+        assert_same(r, want, counts)
+
+
+def test_owned_ranges_concatenate_to_the_whole():
+    rng = random.Random(5)
+    text = rand_dna(rng, 30000)
+    pats = [text[j : j + rng.randint(3, 10)] for j in rng.sample(range(29000), 50)] + [b"ACGTACGT"]
+    d = acg.build(pats)
+    t = acg.pack(to_dev(text))
+    full = acg.scan(d, t, encoding=N.AC_TEXT_PACKED2, n_bases=len(text)).canonical()
+    parts, counts = [], np.zeros(len(pats), np.int64)
+    cuts = [0, 1, 17, 4096, 10000, 29999, 30000]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        r = acg.scan(d, t, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), range_=(a, b))
+        c = r.canonical()
+        ends = c[:, 1] + np.array([len(pats[p]) for p in c[:, 2]]) - 1
+        assert np.all((ends >= a) & (ends < b))
+        parts.append(c)
+        counts += r.counts.cpu().numpy()
+    cat = np.concatenate(parts)
+    cat = cat[np.lexsort((cat[:, 2], cat[:, 1], cat[:, 0]))]
+    assert np.array_equal(cat, full)
+    assert counts.tolist() == np.bincount(full[:, 2], minlength=len(pats)).tolist()
+
+
+def test_host_and_device_buffers_agree():
+    rng = random.Random(6)
+    text = rand_dna(rng, 100000)
+    pats = [text[j : j + 12] for j in range(0, 100000, 997)]
+    d = acg.build(pats)
+    want, counts = oracle_canonical(pats, text)
+    assert_same(acg.scan(d, to_dev(text)), want, counts)  # device ASCII
+    assert_same(acg.scan(d, text), want, counts)  # host ASCII, host results
+    packed_dev = acg.pack(to_dev(text))
+    assert_same(acg.scan(d, packed_dev, encoding=N.AC_TEXT_PACKED2, n_bases=len(text)), want, counts)
+    packed_host = packed_dev.cpu().numpy()
+    assert_same(acg.scan(d, packed_host, encoding=N.AC_TEXT_PACKED2, n_bases=len(text)), want, counts)
+
+
+def test_edge_cases():
+    d = acg.build([b"ACGTACGT", b"A"])
+    r = acg.scan(d, torch.empty(0, dtype=torch.uint8, device=DEV))
+    assert r.n_matches == 0 and r.counts.sum().item() == 0
+    r = acg.scan(d, to_dev(b"ACGTACG"))  # shorter than the long keyword
+    assert sorted(r.pos.tolist()) == [0, 4] and r.counts.tolist() == [0, 2]
+    with pytest.raises(acg.AcError) as e:
+        acg.scan(d, to_dev(b"ACGTTTN"))
+    assert e.value.status == N.AC_ERR_ALPHABET and "offset 6" in str(e.value)
+    r = acg.scan(d, to_dev(b"acgtacgt"), fold_case=True)
+    assert r.counts.tolist() == [1, 2]
+
+
+def test_overflow_reports_exact_count():
+    import ctypes
+
+    d = acg.build([b"A"])
+    t = to_dev(b"A" * 5000)
+    raw = torch.empty((10, 2), dtype=torch.int64, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int64, device=DEV)
+    desc = N.Text(t.data_ptr(), 5000, N.AC_TEXT_ASCII, 1)
+    r = N.Result(raw.data_ptr(), 10, 0, cnt.data_ptr(), 1, 0, 0)
+    st = acg.lib().ac_scan(d.h, ctypes.byref(desc), ctypes.byref(r), None, None, None)
+    assert st == N.AC_ERR_OVERFLOW and r.n_matches == 5000 and cnt.item() == 5000
+    got = sorted(raw[:, 0].tolist())
+    assert len(set(got)) == 10 and all(0 <= g < 5000 for g in got)
+
+
+def test_invalid_arguments():
+    import ctypes
+
+    d = acg.build([b"ACG"])
+    t = to_dev(b"ACGT" * 100)
+    packed = acg.pack(t)
+    mis = N.Text(packed.data_ptr() + 4, 16, N.AC_TEXT_PACKED2, 1)  # not 16-byte aligned
+    r = N.Result()
+    assert acg.lib().ac_scan(d.h, ctypes.byref(mis), ctypes.byref(r), None, None, None) == N.AC_ERR_INVALID_ARG
+    o = N.ScanOpts()
+    o.range_begin, o.range_end, o.hot_states = 10, 5, -1
+    ok = N.Text(t.data_ptr(), 400, N.AC_TEXT_ASCII, 1)
+    assert acg.lib().ac_scan(d.h, ctypes.byref(ok), ctypes.byref(r), ctypes.byref(o), None, None) == N.AC_ERR_INVALID_ARG
+    o.range_begin, o.range_end, o.interleave = 0, 0, 3
+    assert acg.lib().ac_scan(d.h, ctypes.byref(ok), ctypes.byref(r), ctypes.byref(o), None, None) == N.AC_ERR_INVALID_ARG
+
+
+def test_plain_1mbase_uniform_full():
+    """The 1 Mbase i.i.d. workload with 100 keywords of length 8-20, ASCII on the device."""
+    w = synth.plain_small(device="cpu")
+    d = acg.build(w.patterns)
+    want, counts = oracle_canonical(w.patterns, w.text.ascii)
+    r = acg.scan(d, w.text.ascii.to(DEV), stats=True)
+    assert_same(r, want, counts)
+    assert r.stats["scan_ms"] > 0
+
+
+def test_autotune_then_exact():
+    rng = random.Random(9)
+    text = rand_dna(rng, 1 << 20)
+    pats = [text[j : j + 16] for j in rng.sample(range((1 << 20) - 20), 500)]
+    d = acg.build(pats)
+    packed = acg.pack(to_dev(text))
+    best = acg.autotune(d, packed, len(text))
+    assert best["interleave"] in (1, 2, 4, 8) and best["threads"] in (256, 512, 1024)
+    want, counts = oracle_canonical(pats, text)
+    r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), threads=best["threads"],
+                 interleave=best["interleave"], hot_states=best["hot_states"])
+    assert_same(r, want, counts)
