@@ -262,6 +262,14 @@ def run_plain(args, world, rank, local):
     if args.minimal:
         return out, None
 
+    # ---- walk-only ceilings on the same text (no occurrences): the lookup roofline
+    probe = lookup_probe(packed, n)
+    ceiling = probe["uniform100k_default"]["lookups_per_s"]
+    out["roofline"]["lookup"] = {
+        "achieved_lookups_per_s": out["roofline"]["lookups_per_s"], "ceiling_lookups_per_s": ceiling,
+        "frac": round(out["roofline"]["lookups_per_s"] / ceiling, 4),
+        "ceiling_source": "same kernel, same text, 100,000 uniform keywords (no occurrences)", "probe": probe}
+
     # ---- end to end through the public API: host text in, host results out
     host_packed = packed.cpu().pin_memory()
     raw_h = torch.empty((cap, 2), dtype=torch.int64).pin_memory()
@@ -285,6 +293,50 @@ def run_plain(args, world, rank, local):
                   "d2h_bytes_per_step": int(16 * n_matches + 8 * P + 16), "steps": k_e2e}
     del host_packed, raw_h
     return out, (dfa, w, ascii_prefix)
+
+
+# ------------------------------------------------------ lookup roofline
+
+
+def lookup_probe(packed: torch.Tensor, n: int, steps: int = 3) -> dict:
+    """Walk-only ceilings of the scan kernel on the resident text: machines
+    whose keywords (uniform random) essentially never occur, so the time is
+    the dependent table lookups alone. Three placements: a 100,000-keyword
+    machine of the workload's shape (default shared-memory prefix + L2), the
+    same machine entirely through L2, and a 100-keyword machine that fits in
+    shared memory."""
+    import ctypes
+
+    import paper_1403_7294_gb300 as acg
+    from paper_1403_7294_gb300 import _native as N
+    from paper_1403_7294_gb300 import synth
+
+    lib = acg.lib()
+    sp = torch.cuda.current_stream().cuda_stream
+    big = acg.build(synth.uniform_patterns(100_000, 20, 25, synth.BASE_SEED + 77))
+    small = acg.build(synth.uniform_patterns(100, 8, 20, synth.BASE_SEED + 78))
+    desc = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
+    raw = torch.empty((1 << 16, 2), dtype=torch.int64, device="cuda")
+    out = {}
+    for name, d, hot in (("uniform100k_default", big, -1), ("uniform100k_all_l2", big, 0),
+                         ("uniform100_all_smem", small, -1)):
+        o = N.ScanOpts()
+        o.hot_states = hot
+        r = N.Result(raw.data_ptr(), 1 << 16, 0, None, 1, 0, 0)
+        st = N.ScanStats()
+        ms = []
+        for i in range(steps + 1):
+            rc = lib.ac_scan(d.h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(o), sp, ctypes.byref(st))
+            assert rc in (0, N.AC_ERR_OVERFLOW), rc
+            if i:
+                ms.append(st.scan_ms)
+        t = float(np.median(ms))
+        out[name] = {"states": d.info["n_states"], "hot_states": st.hot_states, "occurrences": int(r.n_matches),
+                     "kernel_ms": round(t, 4), "gbases_s": round(n / t / 1e6, 2),
+                     "lookups_per_s": round(st.bases_walked / (t / 1e3), 1)}
+    big.close()
+    small.close()
+    return out
 
 
 # --------------------------------------------------------- CPU baseline

@@ -270,7 +270,7 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     if (!sh.interleave) sh.interleave = 4;
     if (!sh.threads) sh.threads = ac_max_threads(sh.interleave);
     sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave));
-    const uint32_t max_hot = ac_max_hot_states();
+    const uint32_t max_hot = ac_max_hot_states(sh.threads);
     if (!(o && o->hot_states >= 0) && !sh.hot) sh.hot = std::min(h.n_states, max_hot);
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));

@@ -85,8 +85,11 @@ int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t 
                      const unsigned long long* hits, unsigned long long* counts, void* stream);
 // Largest block size the kernels are compiled for at a given interleave.
 uint32_t ac_max_threads(uint32_t interleave);
-// Largest number of states a scan block can stage in shared memory.
-uint32_t ac_max_hot_states();
+// Largest number of states a scan block of `threads` threads can stage in
+// shared memory (next to its per-warp event queues).
+uint32_t ac_max_hot_states(uint32_t threads);
+// Dynamic shared memory of a scan block: hot rows plus event queues.
+size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads);
 // Resident blocks per SM for a shape (occupancy query); 0 on error.
 uint32_t ac_blocks_per_sm(const ScanShape& sh);
 

@@ -90,35 +90,56 @@ struct Sink {
     unsigned long long* hits;
 };
 
-// Warp-cooperative emission. Called by all 32 lanes (warp-uniform branch).
-__device__ __noinline__ void emit_warp(bool mine, uint32_t st, uint64_t end_pos, uint32_t text_id,
-                                       Tables tb, Sink sk) {
-    const int lane = threadIdx.x & 31;
-    uint32_t o0 = 0, k = 0;
-    if (mine) {
-        o0 = tb.out_off[st];
-        k = tb.out_off[st + 1] - o0;
-        atomicAdd(&sk.hits[st], 1ull);
-    }
-    uint32_t incl = k;
+// Hits wait in a per-warp queue in shared memory, 16 B per event:
+// {end position lo, end position hi, state, text id}. Appending costs a
+// ballot and a popc; the queue is expanded into occurrences 32 events at a
+// time, so the global occurrence counter sees one atomicAdd per 32 hits.
+constexpr int QCAP = 64;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Expands the n queued hits of this warp; called by all 32 lanes together.
+// Lanes holding the same state combine their per-state hit counts
+// (__match_any_sync) before one atomicAdd per distinct state.
+__device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink sk) {
+    __syncwarp();
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t b = 0; b < n; b += 32) {
+        const uint32_t i = b + lane;
+        const bool valid = i < n;
+        const uint4 ev = valid ? q[i] : make_uint4(0, 0, 0xffffffffu, 0);
+        const uint32_t st = ev.z;
+        uint32_t o0 = 0, k = 0;
+        if (valid) {
+            o0 = tb.out_off[st];
+            k = tb.out_off[st + 1] - o0;
+        }
+        const uint32_t peers = __match_any_sync(FULL, st);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sk.hits[st], (unsigned long long)__popc(peers));
+        uint32_t incl = k;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t v = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, d);
+            if (lane >= (uint32_t)d) incl += v;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
+        base = __shfl_sync(FULL, base, 31);
+        unsigned long long w = base + (incl - k);
+        const uint64_t end_pos = ((uint64_t)ev.y << 32) | ev.x;
+        for (uint32_t t = 0; t < k; ++t, ++w) {
+            if (w >= sk.capacity) break;
+            const uint32_t pid = tb.out_pid[o0 + t];
+            const uint64_t pos = end_pos + 1 - tb.pat_len[pid];
+            *reinterpret_cast<uint4*>(sk.matches + w) = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev.w);
+        }
     }
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    if (total == 0) return;
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(sk.counter, (unsigned long long)total);
-    base = __shfl_sync(FULL, base, 31);
-    unsigned long long w = base + (incl - k);
-    for (uint32_t i = 0; i < k; ++i, ++w) {
-        if (w >= sk.capacity) break;
-        const uint32_t pid = tb.out_pid[o0 + i];
-        const uint64_t pos = end_pos + 1 - tb.pat_len[pid];
-        uint4 m = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, text_id);
-        *reinterpret_cast<uint4*>(sk.matches + w) = m;
-    }
+    __syncwarp();
 }
 
 // One chain of the walk: a text, the first position read (a multiple of
@@ -155,14 +176,11 @@ struct MaxThreads {
     static constexpr int value = I <= 2 ? 1024 : (I == 4 ? 512 : 256);
 };
 
-__device__ __forceinline__ uint32_t word_of(const uint4& v, int k) {
-    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-
 // Walk I chains in lockstep (all 32 lanes of the warp call this together).
+// q: this warp's event queue in shared memory.
 template <int I>
 __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
-                                     const Tables& tb, const Sink& sk, uint64_t pol_tab, uint64_t pol_txt) {
+                                     const Tables& tb, const Sink& sk, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
     uint32_t nb = 0;
 #pragma unroll
     for (int j = 0; j < I; ++j) {
@@ -170,9 +188,11 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
         nb = b > nb ? b : nb;
     }
     nb = __reduce_max_sync(FULL, nb);
+    const uint32_t lt = lanemask_lt();
     uint32_t s[I];
 #pragma unroll
     for (int j = 0; j < I; ++j) s[j] = 0;
+    uint32_t qn = 0;  // queued events (same value in every lane)
 
     for (uint32_t b = 0; b < nb; ++b) {
         uint4 buf[I];
@@ -184,17 +204,22 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
             buf[j] = act ? load_block(ch[j].text, (ch[j].start >> 4) + 4ull * b, ch[j].nwords, pol_txt)
                          : make_uint4(0, 0, 0, 0);
         }
-#pragma unroll
-        for (int wq = 0; wq < 4; ++wq) {
+#pragma unroll 1
+        for (uint32_t wq = 0; wq < 4; ++wq) {
             uint32_t wd[I];
 #pragma unroll
-            for (int j = 0; j < I; ++j) wd[j] = word_of(buf[j], wq);
+            for (int j = 0; j < I; ++j) {  // next 16 bases; shift the 64-base buffer down
+                wd[j] = buf[j].x;
+                buf[j].x = buf[j].y;
+                buf[j].y = buf[j].z;
+                buf[j].z = buf[j].w;
+            }
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
+            for (int k = 0; k < 16; ++k) {
                 uint32_t e[I];
 #pragma unroll
                 for (int j = 0; j < I; ++j) {
-                    const uint32_t idx = (s[j] << 2) | ((wd[j] >> (2 * q)) & 3u);
+                    const uint32_t idx = (s[j] << 2) | ((wd[j] >> (2 * k)) & 3u);
                     e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta + idx, pol_tab);
                 }
                 uint32_t any = 0;
@@ -204,19 +229,28 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                     any |= e[j] & fmask[j];
                 }
                 if (__any_sync(FULL, any)) {
+                    const uint32_t off = 64u * b + 16u * wq + k;
 #pragma unroll
                     for (int j = 0; j < I; ++j) {
-                        const bool f = (e[j] & fmask[j]) != 0;
-                        if (__any_sync(FULL, f)) {
-                            const uint32_t off = 64u * b + 16 * wq + q;
-                            emit_warp(f && off >= ch[j].lo && off < ch[j].hi, s[j], ch[j].start + off,
-                                      ch[j].text_id, tb, sk);
+                        const bool h = (e[j] & fmask[j]) && off >= ch[j].lo && off < ch[j].hi;
+                        const uint32_t m = __ballot_sync(FULL, h);
+                        if (m) {
+                            if (qn + __popc(m) > (uint32_t)QCAP) {
+                                drain(q, qn, tb, sk);
+                                qn = 0;
+                            }
+                            if (h) {
+                                const uint64_t p = ch[j].start + off;
+                                q[qn + __popc(m & lt)] = make_uint4((uint32_t)p, (uint32_t)(p >> 32), s[j], ch[j].text_id);
+                            }
+                            qn += __popc(m);
                         }
                     }
                 }
             }
         }
     }
+    if (qn) drain(q, qn, tb, sk);
 }
 
 __device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* delta, uint32_t hot) {
@@ -234,6 +268,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nwords = (a.n + 15) >> 4;
@@ -249,7 +284,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
                 idle_chain(ch[j], a.text, nwords, a.text_id);
             }
         }
-        walk<I>(ch, sm, hot, tb, sk, pol_tab, pol_txt);
+        walk<I>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
     }
 }
 
@@ -264,6 +299,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -286,7 +322,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
                 set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
             }
         }
-        walk<I>(ch, sm, hot, tb, sk, pol_tab, pol_txt);
+        walk<I>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
     }
 }
 
@@ -375,15 +411,20 @@ uint32_t ac_max_threads(uint32_t interleave) {
     }
 }
 
-uint32_t ac_max_hot_states() {
+size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads) {
+    return (size_t)hot * 16 + (size_t)(threads / 32) * QCAP * 16;
+}
+
+uint32_t ac_max_hot_states(uint32_t threads) {
     const DeviceProps& p = ac_device_props();
-    return (uint32_t)(p.smem_optin / 16);
+    const size_t queues = ac_scan_smem_bytes(0, threads);
+    return p.smem_optin > queues ? (uint32_t)((p.smem_optin - queues) / 16) : 0u;
 }
 
 namespace {
 template <int I>
 uint32_t occupancy_for(const ScanShape& sh) {
-    const size_t smem = (size_t)sh.hot * 16;
+    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
     if (set_smem(scan_kernel<I>, smem) != 0) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I>, (int)sh.threads, smem) != cudaSuccess)
@@ -418,7 +459,7 @@ int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
     const uint64_t owned = a.own_end > a.own_begin ? a.own_end - a.own_begin : 0;
     if (owned == 0) return 0;
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
-    const size_t smem = (size_t)sh.hot * 16;
+    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
     cudaStream_t st = (cudaStream_t)stream;
     int rc = 0;
 #define LAUNCH(II)                                                                       \
@@ -440,7 +481,7 @@ int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
 
 int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
     if (a.n_items == 0) return 0;
-    const size_t smem = (size_t)sh.hot * 16;
+    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
     cudaStream_t st = (cudaStream_t)stream;
     int rc = 0;
 #define LAUNCH(II)                                                               \
@@ -461,7 +502,7 @@ int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
 }
 
 int ac_prepare_batch(const ScanShape& sh) {
-    const size_t smem = (size_t)sh.hot * 16;
+    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
     switch (sh.interleave) {
         case 1: return set_smem(batch_kernel<1>, smem);
         case 2: return set_smem(batch_kernel<2>, smem);

@@ -125,7 +125,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
         }
     }
     const uint32_t S = dfa->host.n_states;
-    const uint32_t max_hot = std::min(S, ac_max_hot_states());
+    const uint32_t max_hot = std::min(S, ac_max_hot_states(ac_max_threads(4)));
     if (tuning_off() || n == 0) {
         best->interleave = 4;
         best->threads = ac_max_threads(4);
@@ -137,17 +137,17 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     ac_match* d_m = nullptr;
     if (cudaMalloc(&d_m, cap * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
 
-    std::vector<uint32_t> hots = {max_hot};
-    if (max_hot > 1024) hots.push_back(max_hot / 2);
-    if (max_hot > 2048) hots.push_back(max_hot / 4);
     const uint32_t threads_c[] = {256, 512, 1024};
     const uint32_t inter_c[] = {1, 2, 4, 8};
+    const uint32_t frac_c[] = {4, 2, 1};  // shared-memory states: all that fit, 1/2, 1/4
     Entry top{0, 0, 0, 1e30f};
     int rc = AC_OK;
-    for (uint32_t hot : hots)
+    for (uint32_t fr : frac_c)
         for (uint32_t th : threads_c)
             for (uint32_t il : inter_c) {
                 if (th > ac_max_threads(il)) continue;
+                const uint32_t hot = std::min(S, ac_max_hot_states(th)) * fr / 4;
+                if (fr < 4 && hot < 1024) continue;
                 ac_scan_opts o;
                 std::memset(&o, 0, sizeof o);
                 o.threads = th;
