@@ -240,6 +240,42 @@ int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_
 int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* result,
                   const ac_scan_opts* opts /* nullable */, void* stream, ac_scan_stats* stats /* nullable */);
 
+/* ------------------------------------------------------- no-allocation scan
+ * The paper has no counterpart to this call. It exists for callers that
+ * cannot allocate device memory at the moment they scan, for example a
+ * process whose device memory is already held in full by another allocator
+ * (a framework's caching pool that reserved the GPU up front), or a
+ * latency-critical loop that must never enter an allocator. ac_scan takes
+ * its scratch from the stream-ordered pool on every call; this call uses a
+ * fixed scratch array compiled into the library instead and allocates
+ * nothing.
+ *
+ * The scratch array holds AC_NOALLOC_MAX_STATES per-state hit counters plus
+ * a 32-byte counter block (16 MiB + 32 B). It occupies device memory on
+ * every GPU that loads the library, until the process exits, whether or not
+ * this call is used.
+ *
+ * Same semantics as ac_scan, restricted to device-resident inputs/outputs:
+ * text must be AC_TEXT_PACKED2 with on_device = 1; result->on_device must be
+ * 1 (matches and counts in device memory). opts (nullable) as for ac_scan.
+ * Synchronises `stream` once to learn n_matches.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (once per device, with that device current); make that first call
+ * before any stream capture. Every call shares the one array and clears the
+ * part it uses before the scan, so calls that overlap on the GPU (several
+ * streams or host threads at once) race and give undefined results:
+ * serialise them.
+ *
+ * Errors: AC_ERR_TOO_LARGE when the dfa has more than AC_NOALLOC_MAX_STATES
+ * states; AC_ERR_INVALID_ARG for host or ASCII texts, host results or bad
+ * options; AC_ERR_NO_DEVICE; AC_ERR_OVERFLOW as ac_scan; AC_ERR_CUDA.
+ */
+#define AC_NOALLOC_MAX_STATES (1u << 21)
+
+int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,
+                    void* stream);
+
 /* -------------------------------------------------------------- batch plans
  * A batch plan fixes a set of device-resident packed texts and a dfa, and
  * captures the whole batched scan (counter reset, persistent scan, counts)

@@ -30,6 +30,7 @@ AC_BUILD_HOST_ONLY = 2
 AC_TEXT_ASCII = 0
 AC_TEXT_PACKED2 = 1
 AC_SCAN_FOLD_CASE = 1
+AC_NOALLOC_MAX_STATES = 1 << 21
 
 u32, u64, i32, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64
 P = ctypes.c_void_p
@@ -107,6 +108,7 @@ SIGNATURES = {
     "ac_pack": (ctypes.c_int, [P, u64, P, u32, ctypes.POINTER(u64), P]),
     "ac_scan": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,
                                ctypes.POINTER(ScanStats)]),
+    "ac_scan_noalloc": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P]),
     "ac_scan_batch": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
                                      ctypes.POINTER(ScanOpts), P, ctypes.POINTER(ScanStats)]),
     "ac_batch_plan_create": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
