@@ -192,6 +192,9 @@ def run_plain(args, world, rank, local):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
+    t0 = time.time()
+    tuned = acg.autotune(dfa, packed, n)  # cached per (device, machine size, text size); untimed
+    log(f"[bench] autotune {tuned} in {time.time() - t0:.1f}s")
     desc = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
     opts = N.ScanOpts()
     opts.hot_states = -1
@@ -243,6 +246,7 @@ def run_plain(args, world, rank, local):
             "occurrences_per_step": n_matches, "l2": f"inputs larger than L2 ({n // 4 / 1e6:.0f} MB packed text vs 129 MB L2)",
             "parallelism": f"replicas x{world}", "build_ms": round(dfa.info["build_ms"], 1),
             "shape": {k: getattr(stats, k) for k in ("chunk", "threads", "interleave", "hot_states", "grid", "blocks_per_sm")},
+            "autotuned": True,
         },
         "gpu_launches": 2 * args.steps,  # scan kernel + count kernel per step
         "clocks": clk,
@@ -384,7 +388,9 @@ def run_batched(args, steps: int):
     total = int(sum(lens))
     dfa = acg.build(w.patterns)
     packed = [acg.pack(t.contiguous()) for t in w.texts]
-    del w.texts
+    whole = acg.pack(torch.cat([t for t in w.texts]))  # the batch as one text: the tuner's sample
+    acg.autotune(dfa, whole, total)
+    del w.texts, whole
     sp = torch.cuda.current_stream().cuda_stream
     # size outputs
     probe = acg.scan_batch(dfa, packed, encoding=N.AC_TEXT_PACKED2, n_bases=lens, capacity=1 << 20)

@@ -259,25 +259,31 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     const DeviceProps& p = ac_device_props();
     const HostTables& h = dfa->host;
     ScanShape sh;
+    bool tuned_hot_set = false;  // a tuned shape may ask for 0 states in shared memory
     if (!(o && o->chunk && o->threads && o->interleave && o->hot_states >= 0)) {
         ScanShape tuned;
-        if (ac_tuned_lookup(dfa, owned, &tuned)) sh = tuned;
+        if (ac_tuned_lookup(dfa, owned, &tuned)) {
+            sh = tuned;
+            tuned_hot_set = true;
+        }
     }
     if (o && o->threads) sh.threads = o->threads;
     if (o && o->interleave) sh.interleave = o->interleave;
     if (o && o->hot_states >= 0) sh.hot = (uint32_t)o->hot_states;
     if (o && o->chunk) sh.chunk = o->chunk;
-    if (!sh.interleave) sh.interleave = 4;
+    // built-in default (measured best on the benchmark workloads when untuned):
+    // one chain per thread, 1024 threads, half of the shared memory for states
+    if (!sh.interleave) sh.interleave = 1;
     if (!sh.threads) sh.threads = ac_max_threads(sh.interleave);
     sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave));
     const uint32_t max_hot = ac_max_hot_states(sh.threads);
-    if (!(o && o->hot_states >= 0) && !sh.hot) sh.hot = std::min(h.n_states, max_hot);
+    if (!(o && o->hot_states >= 0) && !sh.hot && !tuned_hot_set) sh.hot = std::min(h.n_states, max_hot / 2);
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
     const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
     if (!sh.chunk) {
         const uint64_t halo = h.max_len ? h.max_len - 1 : 0;
-        uint64_t c = round_up((owned + lanes - 1) / std::max<uint64_t>(lanes, 1), 64);
+        uint64_t c = (owned + lanes - 1) / std::max<uint64_t>(lanes, 1);  // one chunk per lane
         c = std::max<uint64_t>(c, std::max<uint64_t>(256, round_up(8 * halo, 64)));
         sh.chunk = (uint32_t)std::min<uint64_t>(c, 1u << 30);
     }

@@ -136,7 +136,8 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
             if (w >= sk.capacity) break;
             const uint32_t pid = tb.out_pid[o0 + t];
             const uint64_t pos = end_pos + 1 - tb.pat_len[pid];
-            *reinterpret_cast<uint4*>(sk.matches + w) = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev.w);
+            // streaming store: occurrences are written once and must not evict table rows from L2
+            __stcs(reinterpret_cast<uint4*>(sk.matches + w), make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev.w));
         }
     }
     __syncwarp();

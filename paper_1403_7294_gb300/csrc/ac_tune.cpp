@@ -10,6 +10,7 @@
 // Environment:
 //   AC_TUNE=off          skip the trials; return the built-in default shape
 //   AC_TUNE_CACHE=path   load tuned shapes from / append them to a JSON file
+//   AC_TUNE_VERBOSE=1    print every candidate's time to stderr
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -125,29 +126,42 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
         }
     }
     const uint32_t S = dfa->host.n_states;
-    const uint32_t max_hot = std::min(S, ac_max_hot_states(ac_max_threads(4)));
-    if (tuning_off() || n == 0) {
-        best->interleave = 4;
-        best->threads = ac_max_threads(4);
-        best->hot_states = (int32_t)max_hot;
+    if (tuning_off() || n == 0) {  // the built-in default shape
+        ScanShape sh = ac_default_shape(dfa, n, nullptr);
+        best->interleave = sh.interleave;
+        best->threads = sh.threads;
+        best->hot_states = (int32_t)sh.hot;
         return AC_OK;
     }
-    // a scratch occurrence buffer so emission costs what it costs in real use
-    const uint64_t cap = std::min<uint64_t>(1u << 22, n / 8 + 1024);
+    // size the occurrence buffer with one counting pass, so every trial writes
+    // all of its occurrences (emission costs what it costs in real use)
+    uint64_t cap = 0;
+    {
+        ac_result r0;
+        std::memset(&r0, 0, sizeof r0);
+        r0.on_device = 1;
+        const int s0 = ac_scan(dfa, sample, &r0, nullptr, stream, nullptr);
+        if (s0 != AC_OK && s0 != AC_ERR_OVERFLOW) return s0;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        cap = std::min<uint64_t>(r0.n_matches + 1024, free_b / 2 / sizeof(ac_match));
+    }
     ac_match* d_m = nullptr;
-    if (cudaMalloc(&d_m, cap * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
+    if (cudaMalloc(&d_m, std::max<uint64_t>(cap, 1) * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
 
     const uint32_t threads_c[] = {256, 512, 1024};
     const uint32_t inter_c[] = {1, 2, 4, 8};
-    const uint32_t frac_c[] = {4, 2, 1};  // shared-memory states: all that fit, 1/2, 1/4
+    const uint32_t frac_c[] = {0, 1, 2, 4};  // shared-memory states: none, 1/4, 1/2, all that fit
     Entry top{0, 0, 0, 1e30f};
     int rc = AC_OK;
+    const char* vb = std::getenv("AC_TUNE_VERBOSE");
+    const bool verbose = vb && vb[0] == '1';
     for (uint32_t fr : frac_c)
         for (uint32_t th : threads_c)
             for (uint32_t il : inter_c) {
                 if (th > ac_max_threads(il)) continue;
-                const uint32_t hot = std::min(S, ac_max_hot_states(th)) * fr / 4;
-                if (fr < 4 && hot < 1024) continue;
+                const uint32_t hot = std::min(S, ac_max_hot_states(th) * fr / 4);
+                if (fr && fr < 4 && hot >= S) continue;  // same as "all" for small machines
                 ac_scan_opts o;
                 std::memset(&o, 0, sizeof o);
                 o.threads = th;
@@ -174,6 +188,9 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
                     if (rep > 0) t_best = std::min(t_best, stt.scan_ms);
                 }
                 if (rc != AC_OK) break;
+                if (verbose)
+                    std::fprintf(stderr, "[ac_autotune] threads=%u interleave=%u hot=%u: %.4f ms\n", th, il, hot,
+                                 t_best);
                 if (t_best < top.ms) top = Entry{th, il, hot, t_best};
             }
     cudaFree(d_m);
