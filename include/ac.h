@@ -69,8 +69,10 @@ typedef struct ac_dfa ac_dfa;
 
 enum ac_build_flags {
     AC_BUILD_FOLD_CASE = 1u, /* accept a,c,g,t in keywords as A,C,G,T                          */
-    AC_BUILD_HOST_ONLY = 2u  /* build the tables on the host only (no GPU needed); such a dfa
+    AC_BUILD_HOST_ONLY = 2u, /* build the tables on the host only (no GPU needed); such a dfa
                                 can be inspected with ac_dfa_tables but not scanned          */
+    AC_BUILD_NO_STRIDE2 = 4u /* skip the two-bases-per-lookup table (saves 64 B per state of
+                                device memory; scans then always read one base per lookup)   */
 };
 
 typedef struct {
@@ -87,8 +89,10 @@ typedef struct {
  * plus the output of the failure state), then the full transition table
  * delta[s][c], c in {A=0,C=1,G=2,T=3}, with states renumbered breadth first
  * (so shallow, frequently visited states have small ids). Unless
- * AC_BUILD_HOST_ONLY is set the tables are copied to the current device
- * (synchronously) and the returned dfa is ready to scan.
+ * AC_BUILD_NO_STRIDE2 is set (or the machine has more than 2^24 states) it
+ * also builds delta2[s][x | y<<2] = delta[delta[s][x]][y], which lets a scan
+ * read two bases per lookup. Unless AC_BUILD_HOST_ONLY is set the tables are
+ * copied to the current device (synchronously) and the dfa is ready to scan.
  * Errors: AC_ERR_INVALID_ARG (NULL pointers, n_patterns == 0),
  * AC_ERR_EMPTY_PATTERN, AC_ERR_ALPHABET (*out untouched), AC_ERR_TOO_LARGE
  * (more than 2^27 states), AC_ERR_OOM, AC_ERR_CUDA.
@@ -110,6 +114,7 @@ typedef struct {
     uint64_t out_entries;  /* total size of all output sets                       */
     uint64_t device_bytes; /* all device memory held by the dfa                   */
     double build_ms;       /* host time of the build (construction + upload)      */
+    uint64_t table2_bytes; /* 64 * S for the two-base table, 0 if not built       */
 } ac_dfa_info_t;
 
 int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
@@ -121,7 +126,10 @@ int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
  *                   out_pid[out_off[s] .. out_off[s+1]);
  *   pat_len[P], pat_state[P]: keyword length and the state where it ends;
  *   depth[S]: distance of each state from the root;
- *   fail[S]: failure state of each state (breadth-first ids). */
+ *   fail[S]: failure state of each state (breadth-first ids);
+ *   delta2[16*s + (x | y<<2)] (NULL if not built): bits 0-29 the state after
+ *                   bases x then y, bit 31 set when that state has output,
+ *                   bit 30 set when the state after x alone has output. */
 typedef struct {
     const uint32_t* delta;
     const uint32_t* out_off;
@@ -130,6 +138,7 @@ typedef struct {
     const uint32_t* pat_state;
     const uint32_t* depth;
     const uint32_t* fail;
+    const uint32_t* delta2;
 } ac_dfa_tables_t;
 
 int ac_dfa_tables(const ac_dfa* dfa, ac_dfa_tables_t* out);
@@ -186,6 +195,9 @@ typedef struct {
                              0..S = exactly that many (breadth-first prefix)    */
     uint32_t flags;       /* ac_scan_flags                                      */
     uint32_t text_id;     /* copied into every ac_match.text_id (ac_scan only)  */
+    uint32_t stride;      /* bases per table lookup: 1, 2 (needs the two-base
+                             table), or 0 = tuned                              */
+    uint32_t reserved;
 } ac_scan_opts;
 
 /* Timing and launch shape of the last scan, filled when requested. */
@@ -195,6 +207,8 @@ typedef struct {
     float pack_ms;       /* device time of the ASCII pack kernel (0 if packed)     */
     float counts_ms;     /* device time of the count kernel                        */
     uint32_t chunk, threads, interleave, hot_states, grid, blocks_per_sm;
+    uint32_t stride;       /* bases per lookup used                                */
+    uint32_t reserved;
     uint64_t bases_walked; /* owned bases plus halo re-reads                       */
 } ac_scan_stats;
 

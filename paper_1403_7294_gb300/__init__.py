@@ -56,13 +56,14 @@ def _as_bytes(p) -> bytes:
 class Dfa:
     """A built machine (ac_build). Immutable; freed with close() or on GC."""
 
-    def __init__(self, patterns: Sequence, fold_case: bool = False, host_only: bool = False):
+    def __init__(self, patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True):
         L = lib()
         self._bufs = [_as_bytes(p) for p in patterns]
         n = len(self._bufs)
         ptrs = (ctypes.c_char_p * max(n, 1))(*self._bufs)
         lens = np.array([len(b) for b in self._bufs], dtype=np.uint32)
-        opts = N.BuildOpts((N.AC_BUILD_FOLD_CASE if fold_case else 0) | (N.AC_BUILD_HOST_ONLY if host_only else 0), 0)
+        opts = N.BuildOpts((N.AC_BUILD_FOLD_CASE if fold_case else 0) | (N.AC_BUILD_HOST_ONLY if host_only else 0)
+                           | (0 if stride2 else N.AC_BUILD_NO_STRIDE2), 0)
         h = ctypes.c_void_p()
         N.check(L.ac_build(ctypes.cast(ptrs, ctypes.c_void_p), lens.ctypes.data, n, ctypes.byref(opts),
                            ctypes.byref(h)), "ac_build")
@@ -86,7 +87,8 @@ class Dfa:
         t = N.DfaTables()
         N.check(lib().ac_dfa_tables(self.h, ctypes.byref(t)), "ac_dfa_tables")
         S, Pn, E = self.info["n_states"], self.info["n_patterns"], self.info["out_entries"]
-        sizes = {"delta": 4 * S, "out_off": S + 1, "out_pid": E, "pat_len": Pn, "pat_state": Pn, "depth": S, "fail": S}
+        sizes = {"delta": 4 * S, "out_off": S + 1, "out_pid": E, "pat_len": Pn, "pat_state": Pn, "depth": S, "fail": S,
+                 "delta2": 16 * S if self.info["table2_bytes"] else 0}
         return {k: np.ctypeslib.as_array(getattr(t, k), shape=(v,)).copy() if v else np.zeros(0, np.uint32)
                 for k, v in sizes.items()}
 
@@ -102,8 +104,8 @@ class Dfa:
             pass
 
 
-def build(patterns: Sequence, fold_case: bool = False, host_only: bool = False) -> Dfa:
-    return Dfa(patterns, fold_case=fold_case, host_only=host_only)
+def build(patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True) -> Dfa:
+    return Dfa(patterns, fold_case=fold_case, host_only=host_only, stride2=stride2)
 
 
 # ------------------------------------------------------------------- texts
@@ -178,10 +180,11 @@ def _split(raw: torch.Tensor, k: int):
     return pos, pid, tid
 
 
-def _opts(range_=None, chunk=0, threads=0, interleave=0, hot_states=-1, fold_case=False, text_id=0):
+def _opts(range_=None, chunk=0, threads=0, interleave=0, hot_states=-1, fold_case=False, text_id=0, stride=0):
     o = N.ScanOpts()
     o.range_begin, o.range_end = (range_ if range_ is not None else (0, 0))
     o.chunk, o.threads, o.interleave, o.hot_states = chunk, threads, interleave, hot_states
+    o.stride = stride
     o.flags = N.AC_SCAN_FOLD_CASE if fold_case else 0
     o.text_id = text_id
     return o
@@ -220,14 +223,14 @@ def _run(fn, dfa, texts_arg, n_texts, capacity, counts, device, opts, stream, wa
 def scan(dfa: Dfa, text, *, encoding: int | None = None, n_bases: int | None = None, capacity: int | None = None,
          counts: bool = True, range_=None, chunk: int = 0, threads: int = 0, interleave: int = 0,
          hot_states: int = -1, fold_case: bool = False, text_id: int = 0, stats: bool = False,
-         stream=None, results_on_device: bool | None = None) -> ScanResult:
+         stream=None, results_on_device: bool | None = None, stride: int = 0) -> ScanResult:
     """One text (ac_scan). text: uint8 ASCII or int32 packed (give n_bases), on CUDA or host."""
     desc, keep = _text_desc(text, encoding, n_bases)
     on_dev = bool(desc.on_device) if results_on_device is None else results_on_device
     device = text.device if isinstance(text, torch.Tensor) and text.is_cuda else torch.device("cuda")
     if capacity is None:
         capacity = max(1024, desc.n_bases // 64)
-    o = _opts(range_, chunk, threads, interleave, hot_states, fold_case, text_id)
+    o = _opts(range_, chunk, threads, interleave, hot_states, fold_case, text_id, stride)
     res = _run(lib().ac_scan, dfa, ctypes.byref(desc), None, capacity, counts, device, o, _stream_ptr(stream),
                stats, on_dev)
     del keep
@@ -237,7 +240,7 @@ def scan(dfa: Dfa, text, *, encoding: int | None = None, n_bases: int | None = N
 def scan_batch(dfa: Dfa, texts: Sequence, *, encoding: int | None = None, n_bases: Sequence[int] | None = None,
                capacity: int | None = None, counts: bool = True, chunk: int = 0, threads: int = 0,
                interleave: int = 0, hot_states: int = -1, fold_case: bool = False, stats: bool = False,
-               stream=None, results_on_device: bool | None = None) -> ScanResult:
+               stream=None, results_on_device: bool | None = None, stride: int = 0) -> ScanResult:
     """Many independent texts in one persistent launch (ac_scan_batch)."""
     descs, keep = [], []
     for i, t in enumerate(texts):
@@ -249,7 +252,7 @@ def scan_batch(dfa: Dfa, texts: Sequence, *, encoding: int | None = None, n_base
     total = sum(d.n_bases for d in descs)
     if capacity is None:
         capacity = max(1024, total // 64)
-    o = _opts(None, chunk, threads, interleave, hot_states, fold_case)
+    o = _opts(None, chunk, threads, interleave, hot_states, fold_case, 0, stride)
     return _run(lib().ac_scan_batch, dfa, arr, len(descs), capacity, counts, torch.device("cuda"), o,
                 _stream_ptr(stream), stats, on_dev)
 
@@ -259,7 +262,7 @@ class BatchPlan:
 
     def __init__(self, dfa: Dfa, packed_texts: Sequence[torch.Tensor], n_bases: Sequence[int], capacity: int,
                  counts: bool = True, chunk: int = 0, threads: int = 0, interleave: int = 0,
-                 hot_states: int = -1, stream=None):
+                 hot_states: int = -1, stream=None, stride: int = 0):
         self.dfa = dfa
         self.texts = list(packed_texts)
         descs = [N.Text(t.data_ptr() if n else None, int(n), N.AC_TEXT_PACKED2, 1)
@@ -270,7 +273,7 @@ class BatchPlan:
         self.raw = torch.empty((max(capacity, 1), 2), dtype=torch.int64, device=dev)
         self.counts = torch.empty(dfa.n_patterns, dtype=torch.int64, device=dev) if counts else None
         r = N.Result(self.raw.data_ptr(), capacity, 0, self.counts.data_ptr() if counts else None, 1, 0, 0)
-        o = _opts(None, chunk, threads, interleave, hot_states)
+        o = _opts(None, chunk, threads, interleave, hot_states, False, 0, stride)
         h = ctypes.c_void_p()
         N.check(lib().ac_batch_plan_create(dfa.h, arr, len(descs), ctypes.byref(r), ctypes.byref(o),
                                            _stream_ptr(stream), ctypes.byref(h)), "ac_batch_plan_create")
@@ -309,7 +312,7 @@ def autotune(dfa: Dfa, packed_sample: torch.Tensor, n_bases: int, stream=None) -
     desc = N.Text(packed_sample.data_ptr(), int(n_bases), N.AC_TEXT_PACKED2, 1)
     o = N.ScanOpts()
     N.check(lib().ac_autotune(dfa.h, ctypes.byref(desc), ctypes.byref(o), _stream_ptr(stream)), "ac_autotune")
-    return {"threads": o.threads, "interleave": o.interleave, "hot_states": o.hot_states}
+    return {"threads": o.threads, "interleave": o.interleave, "hot_states": o.hot_states, "stride": o.stride}
 
 
 # ----------------------------------------------------------------- serving

@@ -27,6 +27,7 @@ AC_ERR_NO_DEVICE = -11
 
 AC_BUILD_FOLD_CASE = 1
 AC_BUILD_HOST_ONLY = 2
+AC_BUILD_NO_STRIDE2 = 4
 AC_TEXT_ASCII = 0
 AC_TEXT_PACKED2 = 1
 AC_SCAN_FOLD_CASE = 1
@@ -44,12 +45,13 @@ class DfaInfo(ctypes.Structure):
     _fields_ = [
         ("n_states", u32), ("n_patterns", u32), ("max_len", u32), ("min_len", u32),
         ("max_depth", u32), ("on_device", u32), ("table_bytes", u64), ("out_entries", u64),
-        ("device_bytes", u64), ("build_ms", ctypes.c_double),
+        ("device_bytes", u64), ("build_ms", ctypes.c_double), ("table2_bytes", u64),
     ]
 
 
 class DfaTables(ctypes.Structure):
-    _fields_ = [(k, ctypes.POINTER(u32)) for k in ("delta", "out_off", "out_pid", "pat_len", "pat_state", "depth", "fail")]
+    _fields_ = [(k, ctypes.POINTER(u32))
+                for k in ("delta", "out_off", "out_pid", "pat_len", "pat_state", "depth", "fail", "delta2")]
 
 
 class Text(ctypes.Structure):
@@ -70,7 +72,8 @@ class Result(ctypes.Structure):
 class ScanOpts(ctypes.Structure):
     _fields_ = [
         ("range_begin", u64), ("range_end", u64), ("chunk", u32), ("threads", u32),
-        ("interleave", u32), ("hot_states", i32), ("flags", u32), ("text_id", u32),
+        ("interleave", u32), ("hot_states", i32), ("flags", u32), ("text_id", u32), ("stride", u32),
+        ("reserved", u32),
     ]
 
 
@@ -78,7 +81,8 @@ class ScanStats(ctypes.Structure):
     _fields_ = [
         ("total_ms", ctypes.c_float), ("scan_ms", ctypes.c_float), ("pack_ms", ctypes.c_float),
         ("counts_ms", ctypes.c_float), ("chunk", u32), ("threads", u32), ("interleave", u32),
-        ("hot_states", u32), ("grid", u32), ("blocks_per_sm", u32), ("bases_walked", u64),
+        ("hot_states", u32), ("grid", u32), ("blocks_per_sm", u32), ("stride", u32), ("reserved", u32),
+        ("bases_walked", u64),
     ]
 
 

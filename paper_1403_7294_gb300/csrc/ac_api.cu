@@ -149,7 +149,8 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
     const uint32_t flags = opts ? opts->flags : 0u;
     ac_dfa* d = new (std::nothrow) ac_dfa();
     if (!d) return AC_ERR_OOM;
-    int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0, &d->host, nullptr);
+    int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0,
+                           (flags & AC_BUILD_NO_STRIDE2) == 0, &d->host, nullptr);
     if (rc != AC_OK) {
         delete d;
         return rc;
@@ -161,9 +162,10 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
             uint32_t** dst;
             const std::vector<uint32_t>* src;
         } ups[] = {{&d->d_delta, &h.delta}, {&d->d_out_off, &h.out_off}, {&d->d_out_pid, &h.out_pid},
-                   {&d->d_pat_len, &h.pat_len}};
+                   {&d->d_pat_len, &h.pat_len}, {&d->d_delta2, &h.delta2}};
         cudaError_t e = cudaSuccess;
         for (auto& u : ups) {
+            if (u.dst == &d->d_delta2 && u.src->empty()) continue;  // two-base table not built
             const size_t bytes = std::max<size_t>(u.src->size(), 1) * sizeof(uint32_t);
             e = dev_alloc((void**)u.dst, bytes);
             if (e != cudaSuccess) break;
@@ -184,12 +186,13 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
 
 extern "C" void ac_free(ac_dfa* d) {
     if (!d) return;
-    if (d->d_delta || d->d_out_off || d->d_out_pid || d->d_pat_len) {
+    if (d->d_delta || d->d_delta2 || d->d_out_off || d->d_out_pid || d->d_pat_len) {
         int cur = 0;
         cudaGetDevice(&cur);
         if (d->device >= 0) cudaSetDevice(d->device);
         cudaDeviceSynchronize();
         cudaFree(d->d_delta);
+        cudaFree(d->d_delta2);
         cudaFree(d->d_out_off);
         cudaFree(d->d_out_pid);
         cudaFree(d->d_pat_len);
@@ -211,6 +214,7 @@ extern "C" int ac_dfa_info(const ac_dfa* d, ac_dfa_info_t* o) {
     o->out_entries = h.out_pid.size();
     o->device_bytes = d->device_bytes;
     o->build_ms = d->build_ms;
+    o->table2_bytes = (uint64_t)h.delta2.size() * 4;
     return AC_OK;
 }
 
@@ -224,6 +228,7 @@ extern "C" int ac_dfa_tables(const ac_dfa* d, ac_dfa_tables_t* o) {
     o->pat_state = h.pat_state.data();
     o->depth = h.depth.data();
     o->fail = h.fail.data();
+    o->delta2 = h.delta2.empty() ? nullptr : h.delta2.data();
     return AC_OK;
 }
 
@@ -269,14 +274,17 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     }
     if (o && o->threads) sh.threads = o->threads;
     if (o && o->interleave) sh.interleave = o->interleave;
+    if (o && o->stride) sh.stride = o->stride;
     if (o && o->hot_states >= 0) sh.hot = (uint32_t)o->hot_states;
     if (o && o->chunk) sh.chunk = o->chunk;
     // built-in default (measured best on the benchmark workloads when untuned):
     // one chain per thread, 1024 threads, half of the shared memory for states
     if (!sh.interleave) sh.interleave = 1;
+    if (!sh.stride || !dfa->d_delta2) sh.stride = 1;
+    if (sh.stride == 2 && sh.interleave > 4) sh.interleave = 4;
     if (!sh.threads) sh.threads = ac_max_threads(sh.interleave);
     sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave));
-    const uint32_t max_hot = ac_max_hot_states(sh.threads);
+    const uint32_t max_hot = ac_max_hot_states(sh.threads, sh.stride);
     if (!(o && o->hot_states >= 0) && !sh.hot && !tuned_hot_set) sh.hot = std::min(h.n_states, max_hot / 2);
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
@@ -301,7 +309,8 @@ bool valid_shape_opts(const ac_scan_opts* o) {
     if (o->threads && (o->threads < 32 || o->threads > 1024 || o->threads % 32)) return false;
     if (o->interleave && o->interleave != 1 && o->interleave != 2 && o->interleave != 4 && o->interleave != 8)
         return false;
-    if (o->threads && o->threads > ac_max_threads(o->interleave ? o->interleave : 4)) return false;
+    if (o->threads && o->threads > ac_max_threads(o->interleave ? o->interleave : 1)) return false;
+    if (o->stride > 2 || (o->stride == 2 && o->interleave == 8)) return false;
     return true;
 }
 
@@ -348,6 +357,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
     const uint64_t n = text->n_bases;
     const uint64_t own_begin = opts ? opts->range_begin : 0;
     const uint64_t own_end = (opts && opts->range_end) ? opts->range_end : n;
@@ -406,6 +416,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
     ScanArgs a;
     a.delta = dfa->d_delta;
+    a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.pat_len = dfa->d_pat_len;
@@ -445,6 +456,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
         stats->hot_states = sh.hot;
         stats->grid = sh.grid;
         stats->blocks_per_sm = sh.blocks_per_sm;
+        stats->stride = sh.stride;
         const uint64_t owned = own_end - own_begin;
         const uint64_t n_chunks = owned ? (owned + sh.chunk - 1) / sh.chunk : 0;
         stats->bases_walked = owned + n_chunks * (uint64_t)(h.max_len - 1);
@@ -493,6 +505,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     const int enc = n_texts ? texts[0].encoding : AC_TEXT_PACKED2;
     const int on_dev = n_texts ? texts[0].on_device : 1;
@@ -589,6 +602,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     }
     BatchArgs a;
     a.delta = dfa->d_delta;
+    a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.pat_len = dfa->d_pat_len;
@@ -627,6 +641,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
         stats->hot_states = sh.hot;
         stats->grid = sh.grid;
         stats->blocks_per_sm = sh.blocks_per_sm;
+        stats->stride = sh.stride;
         stats->bases_walked = total + prefix.back() * (uint64_t)(h.max_len - 1);
     }
     return status;
@@ -667,6 +682,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (!r->on_device || (r->capacity && !r->matches)) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     std::vector<BatchText> bt(n_texts);
     std::vector<uint64_t> lens(n_texts);
@@ -708,6 +724,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
 
     BatchArgs a;
     a.delta = dfa->d_delta;
+    a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.pat_len = dfa->d_pat_len;

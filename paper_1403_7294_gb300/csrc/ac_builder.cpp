@@ -8,6 +8,9 @@
 //          chain (fail(r), fail(fail(r)), ..., root) that has an a-edge, else
 //          the root.
 // output:  the keywords ending at s plus output(fail(s)).
+// stride 2: delta2(s, xy) = delta(delta(s, x), y) for the 16 base pairs, with
+//          one flag for each of the two states entered (a scan that reads two
+//          bases per lookup must still report keywords ending at the first).
 // flatten: delta(s, a) = goto(s, a) if the edge exists, else delta(fail(s), a)
 //          (the root's missing edges loop to the root). Computed breadth
 //          first, so delta(fail(s), .) is final before s is visited. A scan
@@ -41,7 +44,7 @@ inline int base_code(uint8_t c, bool fold) {
 }  // namespace
 
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  HostTables* t, uint32_t* bad_pattern) {
+                  bool with_stride2, HostTables* t, uint32_t* bad_pattern) {
     if (!patterns || !lens || n == 0 || !t) return AC_ERR_INVALID_ARG;
     uint64_t total = 0;
     for (uint32_t p = 0; p < n; ++p) {
@@ -171,6 +174,23 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
         t->pat_len.assign(lens, lens + n);
         t->pat_state.resize(n);
         for (uint32_t p = 0; p < n; ++p) t->pat_state[p] = bfs_id[pat_node[p]];
+
+        // ---- two bases per lookup: delta2[s][x | y << 2] = delta(delta(s, x), y),
+        // bit 31 = the final state has output, bit 30 = the state after x has output
+        t->delta2.clear();
+        if (with_stride2 && (uint64_t)S <= AC_MAX_STATES_STRIDE2) {
+            t->delta2.assign((size_t)S * 16, 0);
+            auto has_out = [&](uint32_t u) { return t->out_off[u + 1] > t->out_off[u]; };
+            for (uint32_t s = 0; s < S; ++s)
+                for (uint32_t x = 0; x < 4; ++x) {
+                    const uint32_t m = t->delta[(size_t)s * 4 + x] & AC_STATE_MASK;
+                    for (uint32_t y = 0; y < 4; ++y) {
+                        const uint32_t f = t->delta[(size_t)m * 4 + y] & AC_STATE_MASK;
+                        t->delta2[(size_t)s * 16 + (x | (y << 2))] =
+                            f | (has_out(f) ? AC_FLAG : 0u) | (has_out(m) ? AC_FLAG_MID : 0u);
+                    }
+                }
+        }
     } catch (const std::bad_alloc&) {
         return AC_ERR_OOM;
     }

@@ -6,14 +6,18 @@
 
 #include "../../include/ac.h"
 
-// Transition entry: bits 0-30 next state, bit 31 "next state has output".
+// Transition entry: low bits next state, bit 31 "next state has output";
+// in the two-base table bit 30 is "the state after the first base has output".
 static constexpr uint32_t AC_FLAG = 0x80000000u;
-static constexpr uint32_t AC_STATE_MASK = 0x7fffffffu;
-static constexpr uint32_t AC_MAX_STATES = 1u << 27;  // 16 B rows stay below 2 GiB
+static constexpr uint32_t AC_FLAG_MID = 0x40000000u;
+static constexpr uint32_t AC_STATE_MASK = 0x3fffffffu;
+static constexpr uint32_t AC_MAX_STATES = 1u << 27;          // 16 B rows stay below 2 GiB
+static constexpr uint32_t AC_MAX_STATES_STRIDE2 = 1u << 24;  // 64 B rows stay below 1 GiB
 
 struct HostTables {
     uint32_t n_states = 0, n_patterns = 0, max_len = 0, min_len = 0, max_depth = 0;
     std::vector<uint32_t> delta;      // [S*4]
+    std::vector<uint32_t> delta2;     // [S*16] two bases per lookup (empty if not built)
     std::vector<uint32_t> out_off;    // [S+1]
     std::vector<uint32_t> out_pid;    // [E]
     std::vector<uint32_t> pat_len;    // [P]
@@ -24,7 +28,7 @@ struct HostTables {
 
 // Builds the flattened machine on the host. Returns an ac_status.
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  HostTables* t, uint32_t* bad_pattern);
+                  bool with_stride2, HostTables* t, uint32_t* bad_pattern);
 
 struct ac_dfa {
     HostTables host;
@@ -32,6 +36,7 @@ struct ac_dfa {
     int device = -1;
     // device tables
     uint32_t* d_delta = nullptr;
+    uint32_t* d_delta2 = nullptr;  // null when the two-base table was not built
     uint32_t* d_out_off = nullptr;
     uint32_t* d_out_pid = nullptr;
     uint32_t* d_pat_len = nullptr;
@@ -42,6 +47,7 @@ struct ac_dfa {
 // ------------------------------------------------------------ launch shapes
 
 struct ScanShape {
+    uint32_t stride = 0;      // bases per lookup: 1 or 2
     uint32_t chunk = 0;       // owned bases per chunk
     uint32_t threads = 0;     // per block
     uint32_t interleave = 0;  // chunks per thread
@@ -62,6 +68,7 @@ const DeviceProps& ac_device_props();
 // Kernel launchers (ac_kernels.cu). All return cudaError_t as int.
 struct ScanArgs {
     const uint32_t* delta;
+    const uint32_t* delta2;  // two-base table (stride 2 only)
     const uint32_t* out_off;
     const uint32_t* out_pid;
     const uint32_t* pat_len;
@@ -85,11 +92,14 @@ int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t 
                      const unsigned long long* hits, unsigned long long* counts, void* stream);
 // Largest block size the kernels are compiled for at a given interleave.
 uint32_t ac_max_threads(uint32_t interleave);
+// Whether kernels exist for an (interleave, stride) pair.
+bool ac_shape_compiled(uint32_t interleave, uint32_t stride);
 // Largest number of states a scan block of `threads` threads can stage in
-// shared memory (next to its per-warp event queues).
-uint32_t ac_max_hot_states(uint32_t threads);
+// shared memory (next to its per-warp event queues); rows are 16 B at
+// stride 1 and 64 B at stride 2.
+uint32_t ac_max_hot_states(uint32_t threads, uint32_t stride);
 // Dynamic shared memory of a scan block: hot rows plus event queues.
-size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads);
+size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads, uint32_t stride);
 // Resident blocks per SM for a shape (occupancy query); 0 on error.
 uint32_t ac_blocks_per_sm(const ScanShape& sh);
 
@@ -100,6 +110,7 @@ struct BatchText {
 };
 struct BatchArgs {
     const uint32_t* delta;
+    const uint32_t* delta2;
     const uint32_t* out_off;
     const uint32_t* out_pid;
     const uint32_t* pat_len;

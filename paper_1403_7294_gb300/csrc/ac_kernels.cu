@@ -2,8 +2,11 @@
 // text over the flattened transition table.
 //
 // Layout in device memory
-//   delta    uint32[S][4]  row s = the 4 transitions of state s (16 B);
-//                          bits 0-30 next state, bit 31 "next state has output"
+//   delta    uint32[S][4]   row s = the 4 transitions of state s (16 B);
+//                           low bits next state, bit 31 "next state has output"
+//   delta2   uint32[S][16]  row s = the 16 two-base transitions (64 B);
+//                           bit 31 "final state has output", bit 30 "state
+//                           after the first base has output"
 //   out_off  uint32[S+1], out_pid uint32[E]: output(s) as CSR
 //   pat_len  uint32[P]
 //   text     uint32[ceil(n/16)] 2-bit packed, base j in bits 2*(j%16) of word j/16
@@ -20,16 +23,18 @@
 // occurrence exactly once.
 //
 // Each thread walks `I` chunks at once (independent dependency chains: their
-// table lookups are in flight together). States [0, hot) - the breadth-first
-// prefix of the machine, i.e. the shallow states most steps visit - are
-// staged in shared memory; the rest are read through L2 with an evict-last
-// policy, while the streamed text uses evict-first.
+// table lookups are in flight together), reading ST bases per lookup (ST = 1:
+// delta; ST = 2: delta2, half the dependent lookups per base). States
+// [0, hot) - the breadth-first prefix of the machine - are staged in shared
+// memory; the rest are read through L1/L2 with an evict-last policy, while
+// the streamed text uses evict-first.
 //
-// Emission: a step whose entry has bit 31 set lands on a state with output.
-// The warp votes; when any lane hit, lanes expand their output sets, a warp
-// prefix sum (shuffles) assigns slots, one lane does a single atomicAdd for
-// the whole warp, and each lane writes its 16-byte occurrences. A per-state
-// hit counter feeds the exact per-keyword counts (kept exact on overflow).
+// Emission: a step whose entry has a flag set lands on a state with output.
+// The warp votes; flagged, owned positions are appended to a per-warp event
+// queue in shared memory (ballot + popc); full queues are expanded 32 events
+// at a time (warp prefix sum, one atomicAdd on the occurrence counter per 32
+// events, 16-byte streaming stores). A per-state hit counter feeds the exact
+// per-keyword counts (kept exact on overflow).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -78,6 +83,7 @@ __device__ __forceinline__ uint4 load_block(const uint32_t* text, uint64_t w, ui
 
 struct Tables {
     const uint32_t* __restrict__ delta;
+    const uint32_t* __restrict__ delta2;
     const uint32_t* __restrict__ out_off;
     const uint32_t* __restrict__ out_pid;
     const uint32_t* __restrict__ pat_len;
@@ -143,6 +149,17 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
     __syncwarp();
 }
 
+// Appends the hits of one ballot (mask m, this lane's flag h) to the queue.
+__device__ __forceinline__ void append(uint4* q, uint32_t& qn, uint32_t m, bool h, uint64_t end_pos, uint32_t st,
+                                       uint32_t text_id, uint32_t lt, const Tables& tb, const Sink& sk) {
+    if (qn + __popc(m) > (uint32_t)QCAP) {
+        drain(q, qn, tb, sk);
+        qn = 0;
+    }
+    if (h) q[qn + __popc(m & lt)] = make_uint4((uint32_t)end_pos, (uint32_t)(end_pos >> 32), st, text_id);
+    qn += __popc(m);
+}
+
 // One chain of the walk: a text, the first position read (a multiple of
 // 64), and the owned end positions [start + lo, start + hi).
 struct Chain {
@@ -177,11 +194,15 @@ struct MaxThreads {
     static constexpr int value = I <= 2 ? 1024 : (I == 4 ? 512 : 256);
 };
 
-// Walk I chains in lockstep (all 32 lanes of the warp call this together).
-// q: this warp's event queue in shared memory.
-template <int I>
+// Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
+// call this together). q: this warp's event queue in shared memory.
+template <int I, int ST>
 __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                      const Tables& tb, const Sink& sk, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
+    constexpr uint32_t ROW_SHIFT = ST == 1 ? 2 : 4;  // log2 entries per row
+    constexpr uint32_t SYM_MASK = ST == 1 ? 3u : 15u;
+    constexpr uint32_t FLAGS = ST == 1 ? AC_FLAG : (AC_FLAG | AC_FLAG_MID);
+    const uint32_t* __restrict__ table = ST == 1 ? tb.delta : tb.delta2;
     uint32_t nb = 0;
 #pragma unroll
     for (int j = 0; j < I; ++j) {
@@ -201,7 +222,7 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
 #pragma unroll
         for (int j = 0; j < I; ++j) {
             const bool act = 64u * b < ch[j].hi;
-            fmask[j] = act ? AC_FLAG : 0u;
+            fmask[j] = act ? FLAGS : 0u;
             buf[j] = act ? load_block(ch[j].text, (ch[j].start >> 4) + 4ull * b, ch[j].nwords, pol_txt)
                          : make_uint4(0, 0, 0, 0);
         }
@@ -216,36 +237,40 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                 buf[j].z = buf[j].w;
             }
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                uint32_t e[I];
+            for (int k = 0; k < 16 / ST; ++k) {
+                uint32_t e[I], sp[I];
 #pragma unroll
                 for (int j = 0; j < I; ++j) {
-                    const uint32_t idx = (s[j] << 2) | ((wd[j] >> (2 * k)) & 3u);
-                    e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta + idx, pol_tab);
+                    const uint32_t idx = (s[j] << ROW_SHIFT) | ((wd[j] >> (2 * ST * k)) & SYM_MASK);
+                    e[j] = (s[j] < hot) ? sm[idx] : ld_table(table + idx, pol_tab);
                 }
                 uint32_t any = 0;
 #pragma unroll
                 for (int j = 0; j < I; ++j) {
+                    sp[j] = s[j];
                     s[j] = e[j] & AC_STATE_MASK;
                     any |= e[j] & fmask[j];
                 }
                 if (__any_sync(FULL, any)) {
-                    const uint32_t off = 64u * b + 16u * wq + k;
+                    const uint32_t off = 64u * b + 16u * wq + ST * k;  // first base of this step
 #pragma unroll
                     for (int j = 0; j < I; ++j) {
-                        const bool h = (e[j] & fmask[j]) && off >= ch[j].lo && off < ch[j].hi;
-                        const uint32_t m = __ballot_sync(FULL, h);
-                        if (m) {
-                            if (qn + __popc(m) > (uint32_t)QCAP) {
-                                drain(q, qn, tb, sk);
-                                qn = 0;
+                        if (ST == 2) {  // a keyword may end at the first base of the pair
+                            const bool hm = (e[j] & fmask[j] & AC_FLAG_MID) && off >= ch[j].lo && off < ch[j].hi;
+                            const uint32_t mm = __ballot_sync(FULL, hm);
+                            if (mm) {
+                                uint32_t smid = 0;
+                                if (hm)
+                                    smid = ld_table(tb.delta + ((sp[j] << 2) | ((wd[j] >> (2 * ST * k)) & 3u)),
+                                                    pol_tab) &
+                                           AC_STATE_MASK;
+                                append(q, qn, mm, hm, ch[j].start + off, smid, ch[j].text_id, lt, tb, sk);
                             }
-                            if (h) {
-                                const uint64_t p = ch[j].start + off;
-                                q[qn + __popc(m & lt)] = make_uint4((uint32_t)p, (uint32_t)(p >> 32), s[j], ch[j].text_id);
-                            }
-                            qn += __popc(m);
                         }
+                        const uint32_t oe = off + ST - 1;  // last base of this step
+                        const bool h = (e[j] & fmask[j] & AC_FLAG) && oe >= ch[j].lo && oe < ch[j].hi;
+                        const uint32_t m = __ballot_sync(FULL, h);
+                        if (m) append(q, qn, m, h, ch[j].start + oe, s[j], ch[j].text_id, lt, tb, sk);
                     }
                 }
             }
@@ -254,22 +279,24 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
     if (qn) drain(q, qn, tb, sk);
 }
 
-__device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* delta, uint32_t hot) {
-    const uint4* g = reinterpret_cast<const uint4*>(delta);
-    for (uint32_t r = threadIdx.x; r < hot; r += blockDim.x) sm_rows[r] = __ldg(g + r);
+// Copies `rows16` 16-byte rows (the hot prefix of the table) to shared memory.
+__device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* table, uint32_t rows16) {
+    const uint4* g = reinterpret_cast<const uint4*>(table);
+    for (uint32_t r = threadIdx.x; r < rows16; r += blockDim.x) sm_rows[r] = __ldg(g + r);
     __syncthreads();
 }
 
-template <int I>
+template <int I, int ST>
 __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
     extern __shared__ uint4 sm_rows[];
-    stage_hot(sm_rows, a.delta, hot);
+    constexpr uint32_t R16 = ST == 1 ? 1 : 4;  // 16-byte units per row
+    stage_hot(sm_rows, ST == 1 ? a.delta : a.delta2, hot * R16);
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
+    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.pat_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
-    uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
+    uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nwords = (a.n + 15) >> 4;
@@ -285,22 +312,23 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
                 idle_chain(ch[j], a.text, nwords, a.text_id);
             }
         }
-        walk<I>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
+        walk<I, ST>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
     }
 }
 
 // Persistent batched scan: warps take 32*I work items at a time from a
 // device cursor; item -> (text, chunk) by binary search over item_prefix.
-template <int I>
+template <int I, int ST>
 __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a, uint32_t hot) {
     extern __shared__ uint4 sm_rows[];
-    stage_hot(sm_rows, a.delta, hot);
+    constexpr uint32_t R16 = ST == 1 ? 1 : 4;
+    stage_hot(sm_rows, ST == 1 ? a.delta : a.delta2, hot * R16);
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.out_off, a.out_pid, a.pat_len};
+    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.pat_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
-    uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
+    uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long base = 0;
@@ -323,7 +351,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
                 set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
             }
         }
-        walk<I>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
+        walk<I, ST>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
     }
 }
 
@@ -379,6 +407,26 @@ int set_smem(K kern, size_t bytes) {
     return (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The (interleave, stride) pairs that are compiled: stride 2 up to interleave 4.
+template <typename F>
+int dispatch(uint32_t interleave, uint32_t stride, F&& f) {
+    if (stride == 1) {
+        switch (interleave) {
+            case 1: return f.template operator()<1, 1>();
+            case 2: return f.template operator()<2, 1>();
+            case 4: return f.template operator()<4, 1>();
+            case 8: return f.template operator()<8, 1>();
+        }
+    } else if (stride == 2) {
+        switch (interleave) {
+            case 1: return f.template operator()<1, 2>();
+            case 2: return f.template operator()<2, 2>();
+            case 4: return f.template operator()<4, 2>();
+        }
+    }
+    return -1;
+}
+
 }  // namespace
 
 const DeviceProps& ac_device_props() {
@@ -412,36 +460,70 @@ uint32_t ac_max_threads(uint32_t interleave) {
     }
 }
 
-size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads) {
-    return (size_t)hot * 16 + (size_t)(threads / 32) * QCAP * 16;
+bool ac_shape_compiled(uint32_t interleave, uint32_t stride) {
+    return (stride == 1 && (interleave == 1 || interleave == 2 || interleave == 4 || interleave == 8)) ||
+           (stride == 2 && (interleave == 1 || interleave == 2 || interleave == 4));
 }
 
-uint32_t ac_max_hot_states(uint32_t threads) {
+size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads, uint32_t stride) {
+    return (size_t)hot * (stride == 2 ? 64 : 16) + (size_t)(threads / 32) * QCAP * 16;
+}
+
+uint32_t ac_max_hot_states(uint32_t threads, uint32_t stride) {
     const DeviceProps& p = ac_device_props();
-    const size_t queues = ac_scan_smem_bytes(0, threads);
-    return p.smem_optin > queues ? (uint32_t)((p.smem_optin - queues) / 16) : 0u;
+    const size_t queues = ac_scan_smem_bytes(0, threads, stride);
+    return p.smem_optin > queues ? (uint32_t)((p.smem_optin - queues) / (stride == 2 ? 64 : 16)) : 0u;
 }
 
 namespace {
-template <int I>
-uint32_t occupancy_for(const ScanShape& sh) {
-    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
-    if (set_smem(scan_kernel<I>, smem) != 0) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I>, (int)sh.threads, smem) != cudaSuccess)
-        return 0;
-    return (uint32_t)nb;
-}
+struct Occupancy {
+    const ScanShape& sh;
+    template <int I, int ST>
+    int operator()() const {
+        const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
+        if (set_smem(scan_kernel<I, ST>, smem) != 0) return 0;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I, ST>, (int)sh.threads, smem) !=
+            cudaSuccess)
+            return 0;
+        return nb;
+    }
+};
+
+struct ScanLaunch {
+    const ScanArgs& a;
+    const ScanShape& sh;
+    uint64_t n_chunks;
+    cudaStream_t st;
+    template <int I, int ST>
+    int operator()() const {
+        const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
+        int rc = set_smem(scan_kernel<I, ST>, smem);
+        if (rc) return rc;
+        scan_kernel<I, ST><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks);
+        return (int)cudaGetLastError();
+    }
+};
+
+struct BatchLaunch {
+    const BatchArgs& a;
+    const ScanShape& sh;
+    cudaStream_t st;
+    bool prepare_only;
+    template <int I, int ST>
+    int operator()() const {
+        const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
+        int rc = set_smem(batch_kernel<I, ST>, smem);
+        if (rc || prepare_only) return rc;
+        batch_kernel<I, ST><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);
+        return (int)cudaGetLastError();
+    }
+};
 }  // namespace
 
 uint32_t ac_blocks_per_sm(const ScanShape& sh) {
-    switch (sh.interleave) {
-        case 1: return occupancy_for<1>(sh);
-        case 2: return occupancy_for<2>(sh);
-        case 4: return occupancy_for<4>(sh);
-        case 8: return occupancy_for<8>(sh);
-        default: return 0;
-    }
+    const int nb = dispatch(sh.interleave, sh.stride ? sh.stride : 1u, Occupancy{sh});
+    return nb > 0 ? (uint32_t)nb : 0u;
 }
 
 int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold, unsigned long long* bad,
@@ -459,58 +541,23 @@ int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold
 int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
     const uint64_t owned = a.own_end > a.own_begin ? a.own_end - a.own_begin : 0;
     if (owned == 0) return 0;
+    if (sh.stride == 2 && !a.delta2) return (int)cudaErrorInvalidValue;
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
-    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = 0;
-#define LAUNCH(II)                                                                       \
-    case II:                                                                             \
-        rc = set_smem(scan_kernel<II>, smem);                                            \
-        if (rc) return rc;                                                               \
-        scan_kernel<II><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks); \
-        break;
-    switch (sh.interleave) {
-        LAUNCH(1)
-        LAUNCH(2)
-        LAUNCH(4)
-        LAUNCH(8)
-        default: return (int)cudaErrorInvalidValue;
-    }
-#undef LAUNCH
-    return (int)cudaGetLastError();
+    const int rc = dispatch(sh.interleave, sh.stride, ScanLaunch{a, sh, n_chunks, (cudaStream_t)stream});
+    return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
 int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
     if (a.n_items == 0) return 0;
-    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = 0;
-#define LAUNCH(II)                                                               \
-    case II:                                                                     \
-        rc = set_smem(batch_kernel<II>, smem);                                   \
-        if (rc) return rc;                                                       \
-        batch_kernel<II><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);          \
-        break;
-    switch (sh.interleave) {
-        LAUNCH(1)
-        LAUNCH(2)
-        LAUNCH(4)
-        LAUNCH(8)
-        default: return (int)cudaErrorInvalidValue;
-    }
-#undef LAUNCH
-    return (int)cudaGetLastError();
+    if (sh.stride == 2 && !a.delta2) return (int)cudaErrorInvalidValue;
+    const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{a, sh, (cudaStream_t)stream, false});
+    return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
 int ac_prepare_batch(const ScanShape& sh) {
-    const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads);
-    switch (sh.interleave) {
-        case 1: return set_smem(batch_kernel<1>, smem);
-        case 2: return set_smem(batch_kernel<2>, smem);
-        case 4: return set_smem(batch_kernel<4>, smem);
-        case 8: return set_smem(batch_kernel<8>, smem);
-        default: return (int)cudaErrorInvalidValue;
-    }
+    BatchArgs dummy{};
+    const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{dummy, sh, nullptr, true});
+    return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
 int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,

@@ -64,7 +64,9 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     if (opts && opts->interleave && opts->interleave != 1 && opts->interleave != 2 && opts->interleave != 4 &&
         opts->interleave != 8)
         return AC_ERR_INVALID_ARG;
-    if (opts && opts->threads && opts->threads > ac_max_threads(opts->interleave ? opts->interleave : 4))
+    if (opts && opts->threads && opts->threads > ac_max_threads(opts->interleave ? opts->interleave : 1))
+        return AC_ERR_INVALID_ARG;
+    if (opts && (opts->stride > 2 || (opts->stride == 2 && (opts->interleave == 8 || !dfa->d_delta2))))
         return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     if (h.n_states > kMaxStates) return AC_ERR_TOO_LARGE;  // the fixed scratch is too small
@@ -87,6 +89,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
     ScanArgs a;
     a.delta = dfa->d_delta;
+    a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.pat_len = dfa->d_pat_len;

@@ -31,7 +31,7 @@ namespace {
 using Key = std::tuple<std::string, uint32_t, uint32_t>;  // device name+sms, log2 S, log2 n
 
 struct Entry {
-    uint32_t threads, interleave, hot;
+    uint32_t threads, interleave, hot, stride;
     float ms;
 };
 
@@ -53,7 +53,7 @@ std::string device_tag() {
 }
 
 // Cache file: one JSON object per line:
-// {"device": "...", "s_class": N, "n_class": N, "threads": N, "interleave": N, "hot": N, "ms": F}
+// {"device": "...", "s_class": N, "n_class": N, "threads": N, "interleave": N, "hot": N, "stride": N, "ms": F}
 void load_file_locked() {
     if (g_loaded) return;
     g_loaded = true;
@@ -63,13 +63,13 @@ void load_file_locked() {
     if (!f) return;
     char line[512], dev[256];
     while (std::fgets(line, sizeof line, f)) {
-        unsigned sc, nc, th, il, hot;
+        unsigned sc, nc, th, il, hot, stride;
         float ms;
         if (std::sscanf(line,
                         " {\"device\": \"%255[^\"]\", \"s_class\": %u, \"n_class\": %u, \"threads\": %u, "
-                        "\"interleave\": %u, \"hot\": %u, \"ms\": %f}",
-                        dev, &sc, &nc, &th, &il, &hot, &ms) == 7)
-            g_cache[Key{dev, sc, nc}] = Entry{th, il, hot, ms};
+                        "\"interleave\": %u, \"hot\": %u, \"stride\": %u, \"ms\": %f}",
+                        dev, &sc, &nc, &th, &il, &hot, &stride, &ms) == 8)
+            g_cache[Key{dev, sc, nc}] = Entry{th, il, hot, stride, ms};
     }
     std::fclose(f);
 }
@@ -81,8 +81,9 @@ void append_file(const Key& k, const Entry& e) {
     if (!f) return;
     std::fprintf(f,
                  "{\"device\": \"%s\", \"s_class\": %u, \"n_class\": %u, \"threads\": %u, \"interleave\": %u, "
-                 "\"hot\": %u, \"ms\": %.6f}\n",
-                 std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), e.threads, e.interleave, e.hot, e.ms);
+                 "\"hot\": %u, \"stride\": %u, \"ms\": %.6f}\n",
+                 std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), e.threads, e.interleave, e.hot, e.stride,
+                 e.ms);
     std::fclose(f);
 }
 
@@ -102,6 +103,7 @@ bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out) {
     out->threads = it->second.threads;
     out->interleave = it->second.interleave;
     out->hot = it->second.hot;
+    out->stride = it->second.stride;
     out->chunk = 0;
     return true;
 }
@@ -122,6 +124,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
             best->threads = it->second.threads;
             best->interleave = it->second.interleave;
             best->hot_states = (int32_t)it->second.hot;
+            best->stride = it->second.stride;
             return AC_OK;
         }
     }
@@ -131,6 +134,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
         best->interleave = sh.interleave;
         best->threads = sh.threads;
         best->hot_states = (int32_t)sh.hot;
+        best->stride = sh.stride;
         return AC_OK;
     }
     // size the occurrence buffer with one counting pass, so every trial writes
@@ -152,25 +156,29 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     const uint32_t threads_c[] = {256, 512, 1024};
     const uint32_t inter_c[] = {1, 2, 4, 8};
     const uint32_t frac_c[] = {0, 1, 2, 4};  // shared-memory states: none, 1/4, 1/2, all that fit
-    Entry top{0, 0, 0, 1e30f};
+    Entry top{0, 0, 0, 0, 1e30f};
     int rc = AC_OK;
     const char* vb = std::getenv("AC_TUNE_VERBOSE");
     const bool verbose = vb && vb[0] == '1';
+    const uint32_t strides = dfa->d_delta2 ? 2u : 1u;
+    for (uint32_t sd = 1; sd <= strides; ++sd)
     for (uint32_t fr : frac_c)
         for (uint32_t th : threads_c)
             for (uint32_t il : inter_c) {
-                if (th > ac_max_threads(il)) continue;
-                const uint32_t hot = std::min(S, ac_max_hot_states(th) * fr / 4);
+                if (th > ac_max_threads(il) || !ac_shape_compiled(il, sd)) continue;
+                const uint32_t hot = std::min(S, ac_max_hot_states(th, sd) * fr / 4);
                 if (fr && fr < 4 && hot >= S) continue;  // same as "all" for small machines
                 ac_scan_opts o;
                 std::memset(&o, 0, sizeof o);
                 o.threads = th;
                 o.interleave = il;
                 o.hot_states = (int32_t)hot;
+                o.stride = sd;
                 ScanShape probe;
                 probe.threads = th;
                 probe.interleave = il;
                 probe.hot = hot;
+                probe.stride = sd;
                 if (ac_blocks_per_sm(probe) == 0) continue;  // does not fit
                 float t_best = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
@@ -189,9 +197,9 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
                 }
                 if (rc != AC_OK) break;
                 if (verbose)
-                    std::fprintf(stderr, "[ac_autotune] threads=%u interleave=%u hot=%u: %.4f ms\n", th, il, hot,
-                                 t_best);
-                if (t_best < top.ms) top = Entry{th, il, hot, t_best};
+                    std::fprintf(stderr, "[ac_autotune] stride=%u threads=%u interleave=%u hot=%u: %.4f ms\n", sd, th,
+                                 il, hot, t_best);
+                if (t_best < top.ms) top = Entry{th, il, hot, sd, t_best};
             }
     cudaFree(d_m);
     if (rc != AC_OK) return rc;
@@ -204,5 +212,6 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     best->threads = top.threads;
     best->interleave = top.interleave;
     best->hot_states = (int32_t)top.hot;
+    best->stride = top.stride;
     return AC_OK;
 }

@@ -56,7 +56,8 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(N.Match) == 16
     assert ctypes.sizeof(N.Text) == 24
     assert ctypes.sizeof(N.Result) == 48
-    assert ctypes.sizeof(N.ScanOpts) == 40
+    assert ctypes.sizeof(N.ScanOpts) == 48
+    assert ctypes.sizeof(N.ScanStats) == 56
 
 
 # ------------------------------------------------------------ validation
@@ -179,6 +180,50 @@ def test_builder_fail_output_depth_match_oracle(seed):
     for p, w in enumerate(pats):
         assert strings[int(t["pat_state"][p])] == w
         assert t["pat_len"][p] == len(w)
+
+
+def walk_pairs(t, text: bytes):
+    """Two bases per lookup over delta2; a keyword ending at the first base of
+    a pair is found through bit 30 and one delta lookup, as the kernel does."""
+    d1, d2, off, pid, plen = t["delta"], t["delta2"], t["out_off"], t["out_pid"], t["pat_len"]
+    s, out = 0, set()
+
+    def emit(state, end):
+        for k in range(off[state], off[state + 1]):
+            p = int(pid[k])
+            out.add((end + 1 - int(plen[p]), p))
+
+    for i in range(0, len(text) - 1, 2):
+        x, y = CODE[text[i]], CODE[text[i + 1]]
+        e = int(d2[16 * s + (x | (y << 2))])
+        if e & (1 << 30):
+            emit(int(d1[4 * s + x]) & 0x3FFFFFFF, i)
+        s = e & 0x3FFFFFFF
+        if e >> 31:
+            emit(s, i + 1)
+    if len(text) % 2:  # odd tail: one single-base step
+        e = int(d1[4 * s + CODE[text[-1]]])
+        s = e & 0x3FFFFFFF
+        if e >> 31:
+            emit(s, len(text) - 1)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_two_base_table_walk_equals_oracle(seed):
+    rng = random.Random(700 + seed)
+    pats = rand_set(rng, rng.randint(1, 50), 1, 9)
+    n = rng.choice([0, 1, 2, 3, 51, 700, 2001])
+    text = bytes(rng.choice(b"ACGT") for _ in range(n)) if seed % 3 else (b"ACG" * n)[:n]
+    t = acg.build(pats, host_only=True).tables()
+    assert len(t["delta2"]) == 16 * len(t["depth"])
+    pos, pid, _ = oracle.Machine(pats).scan(text)
+    assert walk_pairs(t, text) == set(zip(pos.tolist(), pid.tolist()))
+
+
+def test_two_base_table_can_be_skipped():
+    d = acg.build([b"ACGT"], host_only=True, stride2=False)
+    assert d.info["table2_bytes"] == 0 and len(d.tables()["delta2"]) == 0
 
 
 def test_breadth_first_numbering():

@@ -77,7 +77,11 @@ def _cases(seed, k):
         yield pats, text
 
 
-@pytest.mark.parametrize("shape", ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8"])
+SHAPES = ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8",
+          "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1"]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 def test_fuzz_vs_oracle(shape):
     for pats, text in _cases(77, 25):
         lmax = max(len(p) for p in pats)
@@ -91,6 +95,15 @@ def test_fuzz_vs_oracle(shape):
             kw["hot_states"] = 1
         elif shape.startswith("i"):
             kw["interleave"] = int(shape[1:])
+        elif shape.startswith("s"):  # two bases per lookup (s1: one, forced)
+            kw["stride"] = int(shape[1])
+            rest = shape[2:]
+            if rest.startswith("i"):
+                kw["interleave"] = int(rest[1:])
+            elif rest == "hot0":
+                kw["hot_states"] = 0
+            elif rest.startswith("c"):
+                kw["chunk"] = int(rest[1:])
         d = acg.build(pats)
         want, counts = oracle_canonical(pats, text)
         r = acg.scan(d, to_dev(text), capacity=4, **kw)  # tiny capacity: exercises the overflow retry

@@ -35,11 +35,12 @@ def test_chromosome_full_parity():
     d = acg.build(w.patterns)
     packed = acg.pack(w.text.ascii)
     n = w.text.ascii.numel()
-    r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n)
     want, counts = oracle_canonical(w.patterns, w.text.ascii)
-    got = r.canonical()
-    assert got.shape == want.shape and np.array_equal(got, want)
-    assert r.counts.cpu().numpy().tolist() == counts.tolist()
+    for stride in (1, 2):
+        r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, stride=stride)
+        got = r.canonical()
+        assert got.shape == want.shape and np.array_equal(got, want)
+        assert r.counts.cpu().numpy().tolist() == counts.tolist()
     assert r.n_matches > 5000  # the substring half of the keywords occurs
 
 
@@ -57,16 +58,16 @@ def test_genome_sampled_parity_and_invariants():
     assert int(r.counts.sum()) == k
     hist = torch.bincount(r.pattern_id, minlength=len(w.patterns))
     assert torch.equal(hist, r.counts)
-    # the same set under a second launch shape (interleave 1, small chunks, nothing in shared memory)
+    # the same set under a second launch shape (two bases per lookup, small chunks, nothing in shared memory)
     r2 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, chunk=4096,
-                  hot_states=0)
+                  hot_states=0, stride=2)
     assert r2.n_matches == k
     a = torch.sort(_keys(r.pos, r.pattern_id))[0]
     b = torch.sort(_keys(r2.pos, r2.pattern_id))[0]
     assert torch.equal(a, b)
     del r2, b
     assert torch.equal(r.counts, acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=0,
-                                          interleave=2).counts)
+                                          interleave=2, stride=1).counts)
     # sampled windows against the oracle
     end = r.pos + lens[r.pattern_id] - 1
     rng = random.Random(2024)
