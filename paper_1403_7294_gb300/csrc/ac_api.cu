@@ -162,7 +162,7 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
             uint32_t** dst;
             const std::vector<uint32_t>* src;
         } ups[] = {{&d->d_delta, &h.delta}, {&d->d_out_off, &h.out_off}, {&d->d_out_pid, &h.out_pid},
-                   {&d->d_pat_len, &h.pat_len}, {&d->d_delta2, &h.delta2}};
+                   {&d->d_out_len, &h.out_len}, {&d->d_delta2, &h.delta2}};
         cudaError_t e = cudaSuccess;
         for (auto& u : ups) {
             if (u.dst == &d->d_delta2 && u.src->empty()) continue;  // two-base table not built
@@ -186,7 +186,7 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
 
 extern "C" void ac_free(ac_dfa* d) {
     if (!d) return;
-    if (d->d_delta || d->d_delta2 || d->d_out_off || d->d_out_pid || d->d_pat_len) {
+    if (d->d_delta || d->d_delta2 || d->d_out_off || d->d_out_pid || d->d_out_len) {
         int cur = 0;
         cudaGetDevice(&cur);
         if (d->device >= 0) cudaSetDevice(d->device);
@@ -195,7 +195,7 @@ extern "C" void ac_free(ac_dfa* d) {
         cudaFree(d->d_delta2);
         cudaFree(d->d_out_off);
         cudaFree(d->d_out_pid);
-        cudaFree(d->d_pat_len);
+        cudaFree(d->d_out_len);
         cudaSetDevice(cur);
     }
     delete d;
@@ -419,7 +419,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
-    a.pat_len = dfa->d_pat_len;
+    a.out_len = dfa->d_out_len;
     a.n_states = h.n_states;
     a.text = words;
     a.n = n;
@@ -605,7 +605,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
-    a.pat_len = dfa->d_pat_len;
+    a.out_len = dfa->d_out_len;
     a.n_states = h.n_states;
     a.texts = d_bt;
     a.item_prefix = d_prefix;
@@ -727,7 +727,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
-    a.pat_len = dfa->d_pat_len;
+    a.out_len = dfa->d_out_len;
     a.n_states = h.n_states;
     a.texts = p->d_bt;
     a.item_prefix = p->d_prefix;

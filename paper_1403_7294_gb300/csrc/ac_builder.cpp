@@ -174,6 +174,8 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
         t->pat_len.assign(lens, lens + n);
         t->pat_state.resize(n);
         for (uint32_t p = 0; p < n; ++p) t->pat_state[p] = bfs_id[pat_node[p]];
+        t->out_len.resize(E);
+        for (uint64_t k = 0; k < E; ++k) t->out_len[k] = lens[t->out_pid[k]];
 
         // ---- two bases per lookup: delta2[s][x | y << 2] = delta(delta(s, x), y),
         // bit 31 = the final state has output, bit 30 = the state after x has output

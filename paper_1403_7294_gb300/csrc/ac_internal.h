@@ -21,6 +21,7 @@ struct HostTables {
     std::vector<uint32_t> out_off;    // [S+1]
     std::vector<uint32_t> out_pid;    // [E]
     std::vector<uint32_t> pat_len;    // [P]
+    std::vector<uint32_t> out_len;    // [E] pat_len[out_pid[k]]
     std::vector<uint32_t> pat_state;  // [P]
     std::vector<uint32_t> depth;      // [S]
     std::vector<uint32_t> fail;       // [S]
@@ -39,7 +40,7 @@ struct ac_dfa {
     uint32_t* d_delta2 = nullptr;  // null when the two-base table was not built
     uint32_t* d_out_off = nullptr;
     uint32_t* d_out_pid = nullptr;
-    uint32_t* d_pat_len = nullptr;
+    uint32_t* d_out_len = nullptr;  // [E] keyword length of each output entry
     uint64_t device_bytes = 0;
     double build_ms = 0.0;
 };
@@ -71,7 +72,7 @@ struct ScanArgs {
     const uint32_t* delta2;  // two-base table (stride 2 only)
     const uint32_t* out_off;
     const uint32_t* out_pid;
-    const uint32_t* pat_len;
+    const uint32_t* out_len;  // keyword length of each out_pid entry
     uint32_t n_states;
     const uint32_t* text;   // packed words (16-byte aligned)
     uint64_t n;             // bases in the text
@@ -113,7 +114,7 @@ struct BatchArgs {
     const uint32_t* delta2;
     const uint32_t* out_off;
     const uint32_t* out_pid;
-    const uint32_t* pat_len;
+    const uint32_t* out_len;  // keyword length of each out_pid entry
     uint32_t n_states;
     const BatchText* texts;         // [T] device
     const unsigned long long* item_prefix;  // [T+1] device: first work item of each text

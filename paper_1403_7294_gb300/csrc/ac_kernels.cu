@@ -8,7 +8,8 @@
 //                           bit 31 "final state has output", bit 30 "state
 //                           after the first base has output"
 //   out_off  uint32[S+1], out_pid uint32[E]: output(s) as CSR
-//   pat_len  uint32[P]
+//   out_len  uint32[E]     keyword length of each out_pid entry (one load
+//                          gives the start position of an occurrence)
 //   text     uint32[ceil(n/16)] 2-bit packed, base j in bits 2*(j%16) of word j/16
 //
 // Work decomposition (the GPU form of the paper's "approach 1", Sec. IV.A):
@@ -37,7 +38,11 @@
 // per-keyword counts (kept exact on overflow).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ac_internal.h"
 
@@ -86,7 +91,7 @@ struct Tables {
     const uint32_t* __restrict__ delta2;
     const uint32_t* __restrict__ out_off;
     const uint32_t* __restrict__ out_pid;
-    const uint32_t* __restrict__ pat_len;
+    const uint32_t* __restrict__ out_len;  // keyword length of each out_pid entry
 };
 
 struct Sink {
@@ -100,7 +105,13 @@ struct Sink {
 // {end position lo, end position hi, state, text id}. Appending costs a
 // ballot and a popc; the queue is expanded into occurrences 32 events at a
 // time, so the global occurrence counter sees one atomicAdd per 32 hits.
+// A hit at the first base of a two-base step is queued as the state before
+// the step plus that base (EV_MID set); the drain resolves it with one
+// delta lookup, so the walk itself never waits for it.
 constexpr int QCAP = 64;
+constexpr uint32_t EV_MID = 0x80000000u;
+constexpr uint32_t EV_BASE_SHIFT = 29;       // bits 29-30: the first base
+constexpr uint32_t EV_STATE = 0x00ffffffu;  // two-base tables have < 2^24 states
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -118,11 +129,20 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
         const uint32_t i = b + lane;
         const bool valid = i < n;
         const uint4 ev = valid ? q[i] : make_uint4(0, 0, 0xffffffffu, 0);
-        const uint32_t st = ev.z;
+        uint32_t st = ev.z;
+        if (valid && (st & EV_MID)) {  // state after the first base of a pair: one delta lookup
+            st = __ldg(tb.delta + (((st & EV_STATE) << 2) | ((st >> EV_BASE_SHIFT) & 3u))) & AC_STATE_MASK;
+        }
         uint32_t o0 = 0, k = 0;
         if (valid) {
             o0 = tb.out_off[st];
             k = tb.out_off[st + 1] - o0;
+        }
+        // the first keyword's id and length load while the counter atomic is in flight
+        uint32_t pid0 = 0, len0 = 0;
+        if (k) {
+            pid0 = __ldg(tb.out_pid + o0);
+            len0 = __ldg(tb.out_len + o0);
         }
         const uint32_t peers = __match_any_sync(FULL, st);
         if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sk.hits[st], (unsigned long long)__popc(peers));
@@ -140,8 +160,8 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
         const uint64_t end_pos = ((uint64_t)ev.y << 32) | ev.x;
         for (uint32_t t = 0; t < k; ++t, ++w) {
             if (w >= sk.capacity) break;
-            const uint32_t pid = tb.out_pid[o0 + t];
-            const uint64_t pos = end_pos + 1 - tb.pat_len[pid];
+            const uint32_t pid = t ? __ldg(tb.out_pid + o0 + t) : pid0;
+            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0 + t) : len0);
             // streaming store: occurrences are written once and must not evict table rows from L2
             __stcs(reinterpret_cast<uint4*>(sk.matches + w), make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev.w));
         }
@@ -259,12 +279,9 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                             const bool hm = (e[j] & fmask[j] & AC_FLAG_MID) && off >= ch[j].lo && off < ch[j].hi;
                             const uint32_t mm = __ballot_sync(FULL, hm);
                             if (mm) {
-                                uint32_t smid = 0;
-                                if (hm)
-                                    smid = ld_table(tb.delta + ((sp[j] << 2) | ((wd[j] >> (2 * ST * k)) & 3u)),
-                                                    pol_tab) &
-                                           AC_STATE_MASK;
-                                append(q, qn, mm, hm, ch[j].start + off, smid, ch[j].text_id, lt, tb, sk);
+                                const uint32_t pending =
+                                    EV_MID | (((wd[j] >> (2 * ST * k)) & 3u) << EV_BASE_SHIFT) | sp[j];
+                                append(q, qn, mm, hm, ch[j].start + off, pending, ch[j].text_id, lt, tb, sk);
                             }
                         }
                         const uint32_t oe = off + ST - 1;  // last base of this step
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.pat_len};
+    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.out_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -326,7 +343,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.pat_len};
+    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.out_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
@@ -402,9 +419,22 @@ __global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint32
     }
 }
 
+// Raises a kernel's dynamic shared-memory limit to `bytes`; the driver call is
+// skipped when this device already has a limit at least that high for it.
 template <typename K>
 int set_smem(K kern, size_t bytes) {
-    return (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::atomic<int> done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    if ((int)bytes <= done[dev].load(std::memory_order_relaxed)) return 0;
+    const int rc = (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (rc == 0) {
+        int cur = done[dev].load();
+        while ((int)bytes > cur && !done[dev].compare_exchange_weak(cur, (int)bytes)) {
+        }
+    }
+    return rc;
 }
 
 // The (interleave, stride) pairs that are compiled: stride 2 up to interleave 4.
@@ -522,8 +552,24 @@ struct BatchLaunch {
 }  // namespace
 
 uint32_t ac_blocks_per_sm(const ScanShape& sh) {
-    const int nb = dispatch(sh.interleave, sh.stride ? sh.stride : 1u, Occupancy{sh});
-    return nb > 0 ? (uint32_t)nb : 0u;
+    // occupancy depends on (device, interleave, stride, threads, shared memory): memoised
+    static std::mutex mu;
+    static std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, size_t>, uint32_t> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t stride = sh.stride ? sh.stride : 1u;
+    const auto key = std::make_tuple(dev, sh.interleave, stride, sh.threads,
+                                     ac_scan_smem_bytes(sh.hot, sh.threads, stride));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+    }
+    const int nb = dispatch(sh.interleave, stride, Occupancy{sh});
+    const uint32_t r = nb > 0 ? (uint32_t)nb : 0u;
+    std::lock_guard<std::mutex> lk(mu);
+    memo[key] = r;
+    return r;
 }
 
 int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold, unsigned long long* bad,

@@ -92,7 +92,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     a.delta2 = dfa->d_delta2;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
-    a.pat_len = dfa->d_pat_len;
+    a.out_len = dfa->d_out_len;
     a.n_states = h.n_states;
     a.text = (const uint32_t*)text->data;
     a.n = n;

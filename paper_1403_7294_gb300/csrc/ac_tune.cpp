@@ -41,15 +41,26 @@ bool g_loaded = false;
 
 uint32_t size_class(uint64_t x) { return x <= 1 ? 0u : (uint32_t)std::ceil(std::log2((double)x)); }
 
-std::string device_tag() {
+// "<device name>_sm<count>", looked up once per device.
+const std::string& device_tag() {
+    static std::string tags[64];
+    static std::mutex mu;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceProp p;
-    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
-    std::string s = p.name;
-    for (char& c : s)
-        if (c == ' ' || c == '"') c = '_';
-    return s + "_sm" + std::to_string(p.multiProcessorCount);
+    dev &= 63;
+    std::lock_guard<std::mutex> lk(mu);
+    if (tags[dev].empty()) {
+        cudaDeviceProp p;
+        if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+            tags[dev] = "unknown";
+        } else {
+            std::string s = p.name;
+            for (char& c : s)
+                if (c == ' ' || c == '"') c = '_';
+            tags[dev] = s + "_sm" + std::to_string(p.multiProcessorCount);
+        }
+    }
+    return tags[dev];
 }
 
 // Cache file: one JSON object per line:
