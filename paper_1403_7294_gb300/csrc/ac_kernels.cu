@@ -420,19 +420,25 @@ __global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint32
 }
 
 // Raises a kernel's dynamic shared-memory limit to `bytes`; the driver call is
-// skipped when this device already has a limit at least that high for it.
+// skipped when this device already has a limit at least that high for this
+// kernel (keyed by the kernel's address: kernels of one signature share a type).
 template <typename K>
 int set_smem(K kern, size_t bytes) {
-    static std::atomic<int> done[64];
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
     int dev = 0;
     cudaGetDevice(&dev);
-    dev &= 63;
-    if ((int)bytes <= done[dev].load(std::memory_order_relaxed)) return 0;
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = done.find(key);
+        if (it != done.end() && (int)bytes <= it->second) return 0;
+    }
     const int rc = (int)cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (rc == 0) {
-        int cur = done[dev].load();
-        while ((int)bytes > cur && !done[dev].compare_exchange_weak(cur, (int)bytes)) {
-        }
+        std::lock_guard<std::mutex> lk(mu);
+        int& v = done[key];
+        if ((int)bytes > v) v = (int)bytes;
     }
     return rc;
 }
