@@ -76,8 +76,10 @@ enum ac_build_flags {
 };
 
 typedef struct {
-    uint32_t flags; /* ac_build_flags */
-    uint32_t reserved;
+    uint32_t flags;          /* ac_build_flags                                           */
+    uint32_t stride2_states; /* rows of the two-base table: the first (breadth-first, i.e.
+                                shallowest) this many states; 0 = min(S, 2^19). Steps from
+                                deeper states take two one-base lookups instead.          */
 } ac_build_opts;
 
 /*
@@ -89,10 +91,11 @@ typedef struct {
  * plus the output of the failure state), then the full transition table
  * delta[s][c], c in {A=0,C=1,G=2,T=3}, with states renumbered breadth first
  * (so shallow, frequently visited states have small ids). Unless
- * AC_BUILD_NO_STRIDE2 is set (or the machine has more than 2^24 states) it
- * also builds delta2[s][x | y<<2] = delta[delta[s][x]][y], which lets a scan
- * read two bases per lookup. Unless AC_BUILD_HOST_ONLY is set the tables are
- * copied to the current device (synchronously) and the dfa is ready to scan.
+ * AC_BUILD_NO_STRIDE2 is set it also builds delta2[s][x | y<<2] =
+ * delta[delta[s][x]][y] for the shallowest opts->stride2_states states, which
+ * lets a scan read two bases per lookup. Unless AC_BUILD_HOST_ONLY is set the
+ * tables are copied to the current device (synchronously) and the dfa is
+ * ready to scan.
  * Errors: AC_ERR_INVALID_ARG (NULL pointers, n_patterns == 0),
  * AC_ERR_EMPTY_PATTERN, AC_ERR_ALPHABET (*out untouched), AC_ERR_TOO_LARGE
  * (more than 2^27 states), AC_ERR_OOM, AC_ERR_CUDA.
@@ -114,7 +117,7 @@ typedef struct {
     uint64_t out_entries;  /* total size of all output sets                       */
     uint64_t device_bytes; /* all device memory held by the dfa                   */
     double build_ms;       /* host time of the build (construction + upload)      */
-    uint64_t table2_bytes; /* 64 * S for the two-base table, 0 if not built       */
+    uint64_t table2_bytes; /* 64 * rows of the two-base table, 0 if not built     */
 } ac_dfa_info_t;
 
 int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
@@ -127,9 +130,10 @@ int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
  *   pat_len[P], pat_state[P]: keyword length and the state where it ends;
  *   depth[S]: distance of each state from the root;
  *   fail[S]: failure state of each state (breadth-first ids);
- *   delta2[16*s + (x | y<<2)] (NULL if not built): bits 0-29 the state after
- *                   bases x then y, bit 31 set when that state has output,
- *                   bit 30 set when the state after x alone has output. */
+ *   delta2[16*s + (x | y<<2)] for s < table2_bytes/64 (NULL if not built):
+ *                   bits 0-29 the state after bases x then y, bit 31 set when
+ *                   that state has output, bit 30 set when the state after x
+ *                   alone has output. */
 typedef struct {
     const uint32_t* delta;
     const uint32_t* out_off;

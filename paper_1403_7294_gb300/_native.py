@@ -38,7 +38,7 @@ P = ctypes.c_void_p
 
 
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("flags", u32), ("reserved", u32)]
+    _fields_ = [("flags", u32), ("stride2_states", u32)]
 
 
 class DfaInfo(ctypes.Structure):

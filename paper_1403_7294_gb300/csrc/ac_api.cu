@@ -150,7 +150,8 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
     ac_dfa* d = new (std::nothrow) ac_dfa();
     if (!d) return AC_ERR_OOM;
     int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0,
-                           (flags & AC_BUILD_NO_STRIDE2) == 0, &d->host, nullptr);
+                           (flags & AC_BUILD_NO_STRIDE2) == 0, opts ? opts->stride2_states : 0u, &d->host,
+                           nullptr);
     if (rc != AC_OK) {
         delete d;
         return rc;
@@ -214,7 +215,7 @@ extern "C" int ac_dfa_info(const ac_dfa* d, ac_dfa_info_t* o) {
     o->out_entries = h.out_pid.size();
     o->device_bytes = d->device_bytes;
     o->build_ms = d->build_ms;
-    o->table2_bytes = (uint64_t)h.delta2.size() * 4;
+    o->table2_bytes = (uint64_t)h.s2_rows * 64;
     return AC_OK;
 }
 
@@ -287,6 +288,7 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     const uint32_t max_hot = ac_max_hot_states(sh.threads, sh.stride);
     if (!(o && o->hot_states >= 0) && !sh.hot && !tuned_hot_set) sh.hot = std::min(h.n_states, max_hot / 2);
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
+    if (sh.stride == 2) sh.hot = std::min(sh.hot, h.s2_rows);  // staged from the two-base rows
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
     const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
     if (!sh.chunk) {
@@ -417,6 +419,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     ScanArgs a;
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
+    a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.out_len = dfa->d_out_len;
@@ -603,6 +606,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     BatchArgs a;
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
+    a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.out_len = dfa->d_out_len;
@@ -725,6 +729,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     BatchArgs a;
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
+    a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.out_len = dfa->d_out_len;

@@ -44,7 +44,7 @@ inline int base_code(uint8_t c, bool fold) {
 }  // namespace
 
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, HostTables* t, uint32_t* bad_pattern) {
+                  bool with_stride2, uint32_t stride2_states, HostTables* t, uint32_t* bad_pattern) {
     if (!patterns || !lens || n == 0 || !t) return AC_ERR_INVALID_ARG;
     uint64_t total = 0;
     for (uint32_t p = 0; p < n; ++p) {
@@ -180,10 +180,13 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
         // ---- two bases per lookup: delta2[s][x | y << 2] = delta(delta(s, x), y),
         // bit 31 = the final state has output, bit 30 = the state after x has output
         t->delta2.clear();
-        if (with_stride2 && (uint64_t)S <= AC_MAX_STATES_STRIDE2) {
-            t->delta2.assign((size_t)S * 16, 0);
+        t->s2_rows = 0;
+        if (with_stride2) {
+            const uint32_t rows = std::min<uint32_t>(S, stride2_states ? stride2_states : AC_DEFAULT_STRIDE2_ROWS);
+            t->s2_rows = std::min<uint32_t>(rows, AC_MAX_STATES_STRIDE2);
+            t->delta2.assign((size_t)t->s2_rows * 16, 0);
             auto has_out = [&](uint32_t u) { return t->out_off[u + 1] > t->out_off[u]; };
-            for (uint32_t s = 0; s < S; ++s)
+            for (uint32_t s = 0; s < t->s2_rows; ++s)
                 for (uint32_t x = 0; x < 4; ++x) {
                     const uint32_t m = t->delta[(size_t)s * 4 + x] & AC_STATE_MASK;
                     for (uint32_t y = 0; y < 4; ++y) {

@@ -13,11 +13,13 @@ static constexpr uint32_t AC_FLAG_MID = 0x40000000u;
 static constexpr uint32_t AC_STATE_MASK = 0x3fffffffu;
 static constexpr uint32_t AC_MAX_STATES = 1u << 27;          // 16 B rows stay below 2 GiB
 static constexpr uint32_t AC_MAX_STATES_STRIDE2 = 1u << 24;  // 64 B rows stay below 1 GiB
+static constexpr uint32_t AC_DEFAULT_STRIDE2_ROWS = 1u << 19;  // 32 MiB of two-base rows
 
 struct HostTables {
     uint32_t n_states = 0, n_patterns = 0, max_len = 0, min_len = 0, max_depth = 0;
     std::vector<uint32_t> delta;      // [S*4]
-    std::vector<uint32_t> delta2;     // [S*16] two bases per lookup (empty if not built)
+    std::vector<uint32_t> delta2;     // [s2_rows*16] two bases per lookup (empty if not built)
+    uint32_t s2_rows = 0;             // states [0, s2_rows) have two-base rows
     std::vector<uint32_t> out_off;    // [S+1]
     std::vector<uint32_t> out_pid;    // [E]
     std::vector<uint32_t> pat_len;    // [P]
@@ -29,7 +31,7 @@ struct HostTables {
 
 // Builds the flattened machine on the host. Returns an ac_status.
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, HostTables* t, uint32_t* bad_pattern);
+                  bool with_stride2, uint32_t stride2_states, HostTables* t, uint32_t* bad_pattern);
 
 struct ac_dfa {
     HostTables host;
@@ -70,6 +72,7 @@ const DeviceProps& ac_device_props();
 struct ScanArgs {
     const uint32_t* delta;
     const uint32_t* delta2;  // two-base table (stride 2 only)
+    uint32_t s2_rows;        // states with a two-base row
     const uint32_t* out_off;
     const uint32_t* out_pid;
     const uint32_t* out_len;  // keyword length of each out_pid entry
@@ -112,6 +115,7 @@ struct BatchText {
 struct BatchArgs {
     const uint32_t* delta;
     const uint32_t* delta2;
+    uint32_t s2_rows;
     const uint32_t* out_off;
     const uint32_t* out_pid;
     const uint32_t* out_len;  // keyword length of each out_pid entry

@@ -89,6 +89,7 @@ __device__ __forceinline__ uint4 load_block(const uint32_t* text, uint64_t w, ui
 struct Tables {
     const uint32_t* __restrict__ delta;
     const uint32_t* __restrict__ delta2;
+    uint32_t s2_rows;  // states [0, s2_rows) have two-base rows
     const uint32_t* __restrict__ out_off;
     const uint32_t* __restrict__ out_pid;
     const uint32_t* __restrict__ out_len;  // keyword length of each out_pid entry
@@ -111,7 +112,7 @@ struct Sink {
 constexpr int QCAP = 64;
 constexpr uint32_t EV_MID = 0x80000000u;
 constexpr uint32_t EV_BASE_SHIFT = 29;       // bits 29-30: the first base
-constexpr uint32_t EV_STATE = 0x00ffffffu;  // two-base tables have < 2^24 states
+constexpr uint32_t EV_STATE = 0x1fffffffu;  // bits 0-28: the state (machines have < 2^27)
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -261,8 +262,15 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                 uint32_t e[I], sp[I];
 #pragma unroll
                 for (int j = 0; j < I; ++j) {
-                    const uint32_t idx = (s[j] << ROW_SHIFT) | ((wd[j] >> (2 * ST * k)) & SYM_MASK);
-                    e[j] = (s[j] < hot) ? sm[idx] : ld_table(table + idx, pol_tab);
+                    const uint32_t sym = (wd[j] >> (2 * ST * k)) & SYM_MASK;
+                    const uint32_t idx = (s[j] << ROW_SHIFT) | sym;
+                    if (ST == 1 || s[j] < tb.s2_rows) {
+                        e[j] = (s[j] < hot) ? sm[idx] : ld_table(table + idx, pol_tab);
+                    } else {  // deep state without a two-base row: two one-base lookups
+                        const uint32_t e1 = ld_table(tb.delta + ((s[j] << 2) | (sym & 3u)), pol_tab);
+                        const uint32_t e2 = ld_table(tb.delta + (((e1 & AC_STATE_MASK) << 2) | (sym >> 2)), pol_tab);
+                        e[j] = e2 | ((e1 & AC_FLAG) >> 1);  // bit 31: final state, bit 30: after the first base
+                    }
                 }
                 uint32_t any = 0;
 #pragma unroll
@@ -311,7 +319,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.out_len};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -343,7 +351,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.out_off, a.out_pid, a.out_len};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;

@@ -90,6 +90,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     ScanArgs a;
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
+    a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
     a.out_pid = dfa->d_out_pid;
     a.out_len = dfa->d_out_len;

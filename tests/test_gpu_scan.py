@@ -78,14 +78,14 @@ def _cases(seed, k):
 
 
 SHAPES = ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8",
-          "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1"]
+          "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1", "s2rows3", "s2rows40i2"]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 def test_fuzz_vs_oracle(shape):
     for pats, text in _cases(77, 25):
         lmax = max(len(p) for p in pats)
-        kw = {}
+        kw, build_kw = {}, {}
         if shape.startswith("c"):
             kw["chunk"] = {"c1": 1, "c2": 2, "cLm1": max(1, lmax - 1), "cL": lmax, "c97": 97, "c4096": 4096,
                            "cn": max(1, len(text))}[shape]
@@ -98,13 +98,18 @@ def test_fuzz_vs_oracle(shape):
         elif shape.startswith("s"):  # two bases per lookup (s1: one, forced)
             kw["stride"] = int(shape[1])
             rest = shape[2:]
-            if rest.startswith("i"):
+            if rest.startswith("rows"):  # two-base rows only for the shallowest states
+                r_, _, il = rest[4:].partition("i")
+                build_kw["stride2_states"] = int(r_)
+                if il:
+                    kw["interleave"] = int(il)
+            elif rest.startswith("i"):
                 kw["interleave"] = int(rest[1:])
             elif rest == "hot0":
                 kw["hot_states"] = 0
             elif rest.startswith("c"):
                 kw["chunk"] = int(rest[1:])
-        d = acg.build(pats)
+        d = acg.build(pats, **build_kw)
         want, counts = oracle_canonical(pats, text)
         r = acg.scan(d, to_dev(text), capacity=4, **kw)  # tiny capacity: exercises the overflow retry
         assert_same(r, want, counts)
