@@ -294,7 +294,9 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     if (!sh.chunk) {
         const uint64_t halo = h.max_len ? h.max_len - 1 : 0;
         uint64_t c = (owned + lanes - 1) / std::max<uint64_t>(lanes, 1);  // one chunk per lane
-        c = std::max<uint64_t>(c, std::max<uint64_t>(256, round_up(8 * halo, 64)));
+        // short texts: at least 64 owned bases per chunk (walk latency, not halo
+        // re-reads, is what a short text costs)
+        c = std::max<uint64_t>(c, std::max<uint64_t>(64, round_up(halo, 64)));
         sh.chunk = (uint32_t)std::min<uint64_t>(c, 1u << 30);
     }
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;

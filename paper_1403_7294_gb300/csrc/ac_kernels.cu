@@ -109,7 +109,8 @@ struct Sink {
 // A hit at the first base of a two-base step is queued as the state before
 // the step plus that base (EV_MID set); the drain resolves it with one
 // delta lookup, so the walk itself never waits for it.
-constexpr int QCAP = 64;
+constexpr int QCAP = 64;  // = 2 events per lane: drain() takes exactly this many at most
+static_assert(QCAP == 64, "drain() expands at most two events per lane");
 constexpr uint32_t EV_MID = 0x80000000u;
 constexpr uint32_t EV_BASE_SHIFT = 29;       // bits 29-30: the first base
 constexpr uint32_t EV_STATE = 0x1fffffffu;  // bits 0-28: the state (machines have < 2^27)
@@ -120,51 +121,72 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Expands the n queued hits of this warp; called by all 32 lanes together.
-// Lanes holding the same state combine their per-state hit counts
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(FULL, v, d);
+        if (lane >= (uint32_t)d) v += u;
+    }
+    return v;
+}
+
+// Expands the n <= 64 queued hits of this warp; called by all 32 lanes
+// together. Lane l takes events l and l + 32, so every dependent step - the
+// first-base lookup, the output-set bounds, the keyword id/length and the
+// occurrence-counter atomic - is one round trip for the whole queue. Lanes
+// holding the same state combine their per-state hit counts
 // (__match_any_sync) before one atomicAdd per distinct state.
 __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink sk) {
     __syncwarp();
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t b = 0; b < n; b += 32) {
-        const uint32_t i = b + lane;
-        const bool valid = i < n;
-        const uint4 ev = valid ? q[i] : make_uint4(0, 0, 0xffffffffu, 0);
-        uint32_t st = ev.z;
-        if (valid && (st & EV_MID)) {  // state after the first base of a pair: one delta lookup
-            st = __ldg(tb.delta + (((st & EV_STATE) << 2) | ((st >> EV_BASE_SHIFT) & 3u))) & AC_STATE_MASK;
-        }
-        uint32_t o0 = 0, k = 0;
-        if (valid) {
-            o0 = tb.out_off[st];
-            k = tb.out_off[st + 1] - o0;
-        }
-        // the first keyword's id and length load while the counter atomic is in flight
-        uint32_t pid0 = 0, len0 = 0;
-        if (k) {
-            pid0 = __ldg(tb.out_pid + o0);
-            len0 = __ldg(tb.out_len + o0);
-        }
-        const uint32_t peers = __match_any_sync(FULL, st);
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sk.hits[st], (unsigned long long)__popc(peers));
-        uint32_t incl = k;
+    uint4 ev[2];
+    uint32_t st[2], o0[2], k[2], pid0[2], len0[2];
+    bool valid[2];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t v = __shfl_up_sync(FULL, incl, d);
-            if (lane >= (uint32_t)d) incl += v;
-        }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
-        base = __shfl_sync(FULL, base, 31);
-        unsigned long long w = base + (incl - k);
-        const uint64_t end_pos = ((uint64_t)ev.y << 32) | ev.x;
-        for (uint32_t t = 0; t < k; ++t, ++w) {
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t i = 32u * h + lane;
+        valid[h] = i < n;
+        ev[h] = valid[h] ? q[i] : make_uint4(0, 0, 0xffffffffu, 0);
+        st[h] = ev[h].z;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)  // state after the first base of a pair: one delta lookup
+        if (valid[h] && (st[h] & EV_MID))
+            st[h] = __ldg(tb.delta + (((st[h] & EV_STATE) << 2) | ((st[h] >> EV_BASE_SHIFT) & 3u))) & AC_STATE_MASK;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        o0[h] = valid[h] ? __ldg(tb.out_off + st[h]) : 0u;
+        k[h] = valid[h] ? __ldg(tb.out_off + st[h] + 1) - o0[h] : 0u;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // first keyword of each set: loads in flight with the atomic
+        pid0[h] = k[h] ? __ldg(tb.out_pid + o0[h]) : 0u;
+        len0[h] = k[h] ? __ldg(tb.out_len + o0[h]) : 0u;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t peers = __match_any_sync(FULL, st[h]);
+        if (valid[h] && lane == (uint32_t)(__ffs(peers) - 1))
+            atomicAdd(&sk.hits[st[h]], (unsigned long long)__popc(peers));
+    }
+    const uint32_t incl0 = warp_inclusive_sum(k[0], lane);
+    const uint32_t tot0 = __shfl_sync(FULL, incl0, 31);
+    const uint32_t incl1 = warp_inclusive_sum(k[1], lane) + tot0;
+    const uint32_t total = __shfl_sync(FULL, incl1, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned long long w = base + ((h ? incl1 : incl0) - k[h]);
+        const uint64_t end_pos = ((uint64_t)ev[h].y << 32) | ev[h].x;
+        for (uint32_t t = 0; t < k[h]; ++t, ++w) {
             if (w >= sk.capacity) break;
-            const uint32_t pid = t ? __ldg(tb.out_pid + o0 + t) : pid0;
-            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0 + t) : len0);
+            const uint32_t pid = t ? __ldg(tb.out_pid + o0[h] + t) : pid0[h];
+            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0[h] + t) : len0[h]);
             // streaming store: occurrences are written once and must not evict table rows from L2
-            __stcs(reinterpret_cast<uint4*>(sk.matches + w), make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev.w));
+            __stcs(reinterpret_cast<uint4*>(sk.matches + w),
+                   make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev[h].w));
         }
     }
     __syncwarp();
