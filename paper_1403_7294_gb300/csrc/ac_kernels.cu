@@ -234,7 +234,7 @@ __device__ __forceinline__ void idle_chain(Chain& c, const uint32_t* text, uint6
 // Threads per block each interleave factor is compiled for (register budget).
 template <int I>
 struct MaxThreads {
-    static constexpr int value = I <= 2 ? 1024 : (I == 4 ? 512 : 256);
+    static constexpr int value = I == 1 ? 1024 : (I <= 4 ? 512 : 256);
 };
 
 // Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
