@@ -294,6 +294,32 @@ int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_
 int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,
                     void* stream);
 
+/* ---------------------------------------------------------- streaming scans
+ * One long text delivered in consecutive pieces (for example read from a
+ * file block by block: the paper's module reads both the keywords and the
+ * input string from files, Sec. IV.B). Each ac_stream_scan reports the
+ * occurrences whose END lies in that piece, with start positions counted
+ * from the beginning of the whole text; an occurrence that spans a piece
+ * boundary is reported once, by the piece that holds its end. The stream keeps
+ * the last L_max - 1 bases on the device (the state at any position depends
+ * on no more than that). Pieces may be of any length and encoding, host or
+ * device, like ac_scan's text; counts cover the piece's occurrences.
+ * Successive calls on one stream must be issued in order (same CUDA stream or
+ * synchronised); a call that fails - AC_ERR_OVERFLOW included, which still
+ * reports the exact n_matches and counts - leaves the stream unchanged, so the
+ * piece can be sent again (with capacity >= n_matches). */
+
+typedef struct ac_stream ac_stream;
+
+int ac_stream_create(const ac_dfa* dfa, ac_stream** out);
+/* Scans the next piece; opts->range_* are ignored. Errors as ac_scan; on
+ * AC_ERR_ALPHABET bad_offset is relative to the piece. */
+int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* result, const ac_scan_opts* opts /* nullable */,
+                   void* stream, ac_scan_stats* stats /* nullable */);
+/* Forgets the carried bases: the next piece starts a new text at position 0. */
+int ac_stream_reset(ac_stream* s);
+void ac_stream_free(ac_stream* s);
+
 /* -------------------------------------------------------------- batch plans
  * A batch plan fixes a set of device-resident packed texts and a dfa, and
  * captures the whole batched scan (counter reset, persistent scan, counts)

@@ -23,7 +23,7 @@ from . import _native as N
 from ._native import AcError
 
 __all__ = [
-    "Dfa", "ScanResult", "build", "pack", "scan", "scan_batch", "BatchPlan", "autotune", "Server",
+    "Dfa", "ScanResult", "build", "pack", "scan", "scan_batch", "BatchPlan", "Stream", "autotune", "Server",
     "AcError", "lib",
 ]
 
@@ -196,8 +196,8 @@ def _stats_dict(s: N.ScanStats) -> dict:
     return {k: getattr(s, k) for k, _ in N.ScanStats._fields_}
 
 
-def _run(fn, dfa, texts_arg, n_texts, capacity, counts, device, opts, stream, want_stats, on_device=True):
-    """Calls ac_scan / ac_scan_batch, growing the occurrence buffer once on overflow."""
+def _run(fn, dfa, texts_arg, n_texts, capacity, counts, device, opts, stream, want_stats, on_device=True, handle=None):
+    """Calls ac_scan / ac_scan_batch / ac_stream_scan, growing the occurrence buffer once on overflow."""
     cap = capacity
     for attempt in range(2):
         if on_device:
@@ -208,7 +208,7 @@ def _run(fn, dfa, texts_arg, n_texts, capacity, counts, device, opts, stream, wa
             cnt = torch.empty(dfa.n_patterns, dtype=torch.int64).pin_memory() if counts else None
         r = N.Result(raw.data_ptr(), cap, 0, cnt.data_ptr() if cnt is not None else None, int(on_device), 0, 0)
         stt = N.ScanStats()
-        args = (dfa.h, texts_arg) + ((n_texts,) if n_texts is not None else ())
+        args = (handle if handle is not None else dfa.h, texts_arg) + ((n_texts,) if n_texts is not None else ())
         st = fn(*args, ctypes.byref(r), ctypes.byref(opts), stream, ctypes.byref(stt) if want_stats else None)
         if st == N.AC_ERR_OVERFLOW and attempt == 0:
             cap = int(r.n_matches)
@@ -301,6 +301,47 @@ class BatchPlan:
     def close(self):
         if getattr(self, "h", None):
             lib().ac_batch_plan_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """One long text scanned in consecutive pieces (ac_stream_*): positions are
+    global, and an occurrence spanning a piece boundary is reported once, by
+    the piece that holds its end."""
+
+    def __init__(self, dfa: Dfa):
+        h = ctypes.c_void_p()
+        N.check(lib().ac_stream_create(dfa.h, ctypes.byref(h)), "ac_stream_create")
+        self.h = h
+        self.dfa = dfa
+
+    def scan(self, piece, *, encoding: int | None = None, n_bases: int | None = None, capacity: int | None = None,
+             counts: bool = True, chunk: int = 0, threads: int = 0, interleave: int = 0, hot_states: int = -1,
+             fold_case: bool = False, stats: bool = False, stream=None, results_on_device: bool | None = None,
+             stride: int = 0) -> ScanResult:
+        desc, keep = _text_desc(piece, encoding, n_bases)
+        on_dev = bool(desc.on_device) if results_on_device is None else results_on_device
+        device = piece.device if isinstance(piece, torch.Tensor) and piece.is_cuda else torch.device("cuda")
+        if capacity is None:
+            capacity = max(1024, desc.n_bases // 64)
+        o = _opts(None, chunk, threads, interleave, hot_states, fold_case, 0, stride)
+        res = _run(lib().ac_stream_scan, self.dfa, ctypes.byref(desc), None, capacity, counts, device, o,
+                   _stream_ptr(stream), stats, on_dev, handle=self.h)
+        del keep
+        return res
+
+    def reset(self):
+        N.check(lib().ac_stream_reset(self.h), "ac_stream_reset")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ac_stream_free(self.h)
             self.h = None
 
     def __del__(self):

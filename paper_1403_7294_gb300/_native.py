@@ -115,6 +115,11 @@ SIGNATURES = {
     "ac_scan_noalloc": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P]),
     "ac_scan_batch": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
                                      ctypes.POINTER(ScanOpts), P, ctypes.POINTER(ScanStats)]),
+    "ac_stream_create": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+    "ac_stream_scan": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,
+                                      ctypes.POINTER(ScanStats)]),
+    "ac_stream_reset": (ctypes.c_int, [P]),
+    "ac_stream_free": (None, [P]),
     "ac_batch_plan_create": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
                                             ctypes.POINTER(ScanOpts), P, ctypes.POINTER(P)]),
     "ac_batch_plan_run": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.POINTER(Result)]),

@@ -348,6 +348,103 @@ int finish(cudaStream_t st, const unsigned long long* d_counter, const unsigned 
     return nm > r->capacity ? AC_ERR_OVERFLOW : AC_OK;
 }
 
+// The scan over device-resident packed words, the count kernel and the final
+// read of the occurrence count (events 3..6 of `ev`; 0..2 are the caller's).
+int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own_begin, uint64_t own_end,
+              uint64_t pos_offset, ac_result* r, const ac_scan_opts* opts, cudaStream_t st, Scratch& sc,
+              unsigned long long* d_ctr, unsigned long long* d_hits, bool check_alphabet, Events& ev,
+              ac_scan_stats* stats) {
+    const HostTables& h = dfa->host;
+    cudaError_t e;
+    // ---- outputs
+    ac_match* d_matches = r->matches;
+    unsigned long long* d_counts = (unsigned long long*)r->counts;
+    if (!r->on_device) {
+        if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
+        if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    // ---- the scan
+    const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
+    ScanArgs a;
+    a.delta = dfa->d_delta;
+    a.delta2 = dfa->d_delta2;
+    a.s2_rows = h.s2_rows;
+    a.out_off = dfa->d_out_off;
+    a.out_pid = dfa->d_out_pid;
+    a.out_len = dfa->d_out_len;
+    a.n_states = h.n_states;
+    a.text = words;
+    a.n = n;
+    a.own_begin = own_begin;
+    a.own_end = own_end;
+    a.halo = h.max_len - 1;
+    a.text_id = opts ? opts->text_id : 0u;
+    a.matches = d_matches;
+    a.capacity = r->capacity;
+    a.counter = d_ctr;
+    a.hits = d_hits;
+    a.pos_offset = pos_offset;
+    ev.rec(3);
+    int rc = ac_launch_scan(a, sh, st);
+    if (rc) return cuda_status((cudaError_t)rc);
+    ev.rec(4);
+    if (d_counts) {
+        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
+        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, st);
+        if (rc) return cuda_status((cudaError_t)rc);
+    }
+    ev.rec(5);
+    const int status = finish(st, d_ctr, check_alphabet ? d_ctr + 2 : nullptr, r, d_matches, d_counts, h.n_patterns);
+    ev.rec(6);
+    if (stats) {
+        cudaEventSynchronize(ev.ev[6]);
+        stats->total_ms = ev.ms(0, 6);
+        stats->pack_ms = ev.ms(1, 2);
+        stats->scan_ms = ev.ms(3, 4);
+        stats->counts_ms = ev.ms(4, 5);
+        stats->chunk = sh.chunk;
+        stats->threads = sh.threads;
+        stats->interleave = sh.interleave;
+        stats->hot_states = sh.hot;
+        stats->grid = sh.grid;
+        stats->blocks_per_sm = sh.blocks_per_sm;
+        stats->stride = sh.stride;
+        const uint64_t owned = own_end - own_begin;
+        const uint64_t n_chunks = owned ? (owned + sh.chunk - 1) / sh.chunk : 0;
+        stats->bases_walked = owned + n_chunks * (uint64_t)(h.max_len - 1);
+    }
+    return status;
+}
+
+// Brings a text onto the device as packed words (staging host data through
+// scratch, packing ASCII with the alphabet check into bad).
+int stage_packed(const ac_text* text, uint32_t fold, cudaStream_t st, Scratch& sc, unsigned long long* bad,
+                 const uint32_t** words) {
+    cudaError_t e;
+    const uint64_t n = text->n_bases;
+    const void* src = text->data;
+    *words = nullptr;
+    if (!n) return AC_OK;
+    if (!text->on_device) {
+        void* d_src = nullptr;
+        if ((e = sc.get(&d_src, round_up(text_bytes(*text), 16))) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(d_src, text->data, text_bytes(*text), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_status(e);
+        src = d_src;
+    }
+    if (text->encoding == AC_TEXT_ASCII) {
+        uint32_t* d_packed = nullptr;
+        if ((e = sc.get((void**)&d_packed, round_up((n + 15) / 16 * 4, 16))) != cudaSuccess) return cuda_status(e);
+        const int rc = ac_launch_pack((const uint8_t*)src, n, d_packed, fold != 0, bad, st);
+        if (rc) return cuda_status((cudaError_t)rc);
+        *words = d_packed;
+    } else {
+        *words = (const uint32_t*)src;
+    }
+    return AC_OK;
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------- scan
@@ -406,66 +503,107 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
         words = (const uint32_t*)src;
     }
     ev.rec(2);
+    return scan_core(dfa, words, n, own_begin, own_end, 0, r, opts, st, sc, d_ctr, d_hits,
+                     text->encoding == AC_TEXT_ASCII, ev, stats);
+}
 
-    // ---- outputs
-    ac_match* d_matches = r->matches;
-    unsigned long long* d_counts = (unsigned long long*)r->counts;
-    if (!r->on_device) {
-        if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
-        if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess)
-            return cuda_status(e);
-    }
+// --------------------------------------------------------------- streaming
+// A text delivered in consecutive pieces. The stream keeps the last L_max - 1
+// bases seen (the longest state string any position can depend on); each
+// piece is spliced behind them and scanned owning only the piece's own end
+// positions, so occurrences spanning a piece boundary are reported once, with
+// global start positions.
 
-    // ---- the scan
-    const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
-    ScanArgs a;
-    a.delta = dfa->d_delta;
-    a.delta2 = dfa->d_delta2;
-    a.s2_rows = h.s2_rows;
-    a.out_off = dfa->d_out_off;
-    a.out_pid = dfa->d_out_pid;
-    a.out_len = dfa->d_out_len;
-    a.n_states = h.n_states;
-    a.text = words;
-    a.n = n;
-    a.own_begin = own_begin;
-    a.own_end = own_end;
-    a.halo = h.max_len - 1;
-    a.text_id = opts ? opts->text_id : 0u;
-    a.matches = d_matches;
-    a.capacity = r->capacity;
-    a.counter = d_ctr;
-    a.hits = d_hits;
-    ev.rec(3);
-    int rc = ac_launch_scan(a, sh, stream);
-    if (rc) return cuda_status((cudaError_t)rc);
-    ev.rec(4);
-    if (d_counts) {
-        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
-        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, stream);
-        if (rc) return cuda_status((cudaError_t)rc);
+struct ac_stream {
+    const ac_dfa* dfa = nullptr;
+    int device = 0;
+    uint32_t* d_carry = nullptr;  // packed, carry_cap bases
+    uint64_t carry_cap = 0;
+    uint64_t carry_n = 0;         // bases held (<= L_max - 1)
+    uint64_t consumed = 0;        // bases of the text before the next piece
+};
+
+extern "C" int ac_stream_create(const ac_dfa* dfa, ac_stream** out) {
+    if (!dfa || !out) return AC_ERR_INVALID_ARG;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    ac_stream* s = new (std::nothrow) ac_stream();
+    if (!s) return AC_ERR_OOM;
+    s->dfa = dfa;
+    cudaGetDevice(&s->device);
+    s->carry_cap = round_up(std::max<uint64_t>(dfa->host.max_len, 16), 16);
+    const cudaError_t e = dev_alloc((void**)&s->d_carry, s->carry_cap / 4 + 16);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_status(e);
     }
-    ev.rec(5);
-    int status = finish(st, d_ctr, text->encoding == AC_TEXT_ASCII ? d_ctr + 2 : nullptr, r, d_matches, d_counts,
-                        h.n_patterns);
-    ev.rec(6);
-    if (stats) {
-        cudaEventSynchronize(ev.ev[6]);
-        stats->total_ms = ev.ms(0, 6);
-        stats->pack_ms = ev.ms(1, 2);
-        stats->scan_ms = ev.ms(3, 4);
-        stats->counts_ms = ev.ms(4, 5);
-        stats->chunk = sh.chunk;
-        stats->threads = sh.threads;
-        stats->interleave = sh.interleave;
-        stats->hot_states = sh.hot;
-        stats->grid = sh.grid;
-        stats->blocks_per_sm = sh.blocks_per_sm;
-        stats->stride = sh.stride;
-        const uint64_t owned = own_end - own_begin;
-        const uint64_t n_chunks = owned ? (owned + sh.chunk - 1) / sh.chunk : 0;
-        stats->bases_walked = owned + n_chunks * (uint64_t)(h.max_len - 1);
-    }
+    *out = s;
+    return AC_OK;
+}
+
+extern "C" int ac_stream_reset(ac_stream* s) {
+    if (!s) return AC_ERR_INVALID_ARG;
+    s->carry_n = 0;
+    s->consumed = 0;
+    return AC_OK;
+}
+
+extern "C" void ac_stream_free(ac_stream* s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    cudaFree(s->d_carry);
+    delete s;
+}
+
+extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, const ac_scan_opts* opts, void* stream,
+                              ac_scan_stats* stats) {
+    if (!s || !piece || !r) return AC_ERR_INVALID_ARG;
+    r->bad_offset = ~0ull;
+    const ac_dfa* dfa = s->dfa;
+    if (piece->encoding != AC_TEXT_ASCII && piece->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    if (piece->n_bases && !piece->data) return AC_ERR_INVALID_ARG;
+    if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
+    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
+    if (piece->on_device && piece->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(piece->data) & 15))
+        return AC_ERR_INVALID_ARG;
+    const HostTables& h = dfa->host;
+    const uint64_t n = piece->n_bases;
+    const uint64_t total = s->carry_n + n;
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    Events ev(stats != nullptr, st);
+    Scratch sc(st);
+    cudaError_t e;
+    ev.rec(0);
+    unsigned long long* d_ctr = nullptr;  // [0] occurrences [1] cursor [2] bad offset [3] pad
+    unsigned long long* d_hits = nullptr;
+    if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
+    ev.rec(1);
+    const uint32_t* pw = nullptr;
+    int rc = stage_packed(piece, fold, st, sc, d_ctr + 2, &pw);
+    if (rc != AC_OK) return rc;
+    // carry ++ piece, bit-exact at any base offset
+    uint32_t* comb = nullptr;
+    if ((e = sc.get((void**)&comb, round_up((total + 15) / 16 * 4, 16) + 16)) != cudaSuccess) return cuda_status(e);
+    if ((rc = ac_launch_splice(comb, 0, s->d_carry, 0, s->carry_n, st)) != 0) return cuda_status((cudaError_t)rc);
+    if ((rc = ac_launch_splice(comb, s->carry_n, pw, 0, n, st)) != 0) return cuda_status((cudaError_t)rc);
+    ev.rec(2);
+    const int status = scan_core(dfa, comb, total, s->carry_n, total, s->consumed - s->carry_n, r, opts, st, sc, d_ctr,
+                                 d_hits, piece->encoding == AC_TEXT_ASCII, ev, stats);
+    // on any error (overflow included) the stream is unchanged and the piece can
+    // be sent again (an alphabet error's bad_offset is relative to the piece)
+    if (status != AC_OK) return status;
+    // the last L_max - 1 bases become the carry of the next piece
+    const uint64_t keep = std::min<uint64_t>(total, h.max_len ? h.max_len - 1 : 0);
+    if ((rc = ac_launch_splice(s->d_carry, 0, comb, total - keep, keep, st)) != 0) return cuda_status((cudaError_t)rc);
+    s->carry_n = keep;
+    s->consumed += n;
     return status;
 }
 

@@ -87,6 +87,7 @@ struct ScanArgs {
     uint64_t capacity;
     unsigned long long* counter;  // [0] = occurrences
     unsigned long long* hits;     // [S] flagged steps per state
+    uint64_t pos_offset;          // added to every reported start position
 };
 
 int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold,
@@ -94,6 +95,9 @@ int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold
 int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream);
 int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,
                      const unsigned long long* hits, unsigned long long* counts, void* stream);
+// Copies n packed bases from base src_off of src to base dst_off of dst.
+int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
+                     void* stream);
 // Largest block size the kernels are compiled for at a given interleave.
 uint32_t ac_max_threads(uint32_t interleave);
 // Whether kernels exist for an (interleave, stride) pair.

@@ -100,17 +100,19 @@ struct Sink {
     uint64_t capacity;
     unsigned long long* counter;
     unsigned long long* hits;
+    uint64_t pos_offset;  // added to every reported start (streaming scans)
 };
 
 // Hits wait in a per-warp queue in shared memory, 16 B per event:
 // {end position lo, end position hi, state, text id}. Appending costs a
-// ballot and a popc; the queue is expanded into occurrences 32 events at a
-// time, so the global occurrence counter sees one atomicAdd per 32 hits.
+// ballot and a popc; the queue is expanded into occurrences QCAP events at
+// a time, so the global occurrence counter sees one atomicAdd per QCAP hits.
 // A hit at the first base of a two-base step is queued as the state before
 // the step plus that base (EV_MID set); the drain resolves it with one
 // delta lookup, so the walk itself never waits for it.
-constexpr int QCAP = 64;  // = 2 events per lane: drain() takes exactly this many at most
-static_assert(QCAP == 64, "drain() expands at most two events per lane");
+constexpr int QCAP = 128;     // events per warp queue
+constexpr int EPL = QCAP / 32;  // events each lane expands in drain()
+static_assert(QCAP % 32 == 0, "whole events per lane");
 constexpr uint32_t EV_MID = 0x80000000u;
 constexpr uint32_t EV_BASE_SHIFT = 29;       // bits 29-30: the first base
 constexpr uint32_t EV_STATE = 0x1fffffffu;  // bits 0-28: the state (machines have < 2^27)
@@ -130,8 +132,8 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane
     return v;
 }
 
-// Expands the n <= 64 queued hits of this warp; called by all 32 lanes
-// together. Lane l takes events l and l + 32, so every dependent step - the
+// Expands the n <= QCAP queued hits of this warp; called by all 32 lanes
+// together. Lane l takes events l, l + 32, ..., so every dependent step - the
 // first-base lookup, the output-set bounds, the keyword id/length and the
 // occurrence-counter atomic - is one round trip for the whole queue. Lanes
 // holding the same state combine their per-state hit counts
@@ -139,51 +141,54 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane
 __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink sk) {
     __syncwarp();
     const uint32_t lane = threadIdx.x & 31;
-    uint4 ev[2];
-    uint32_t st[2], o0[2], k[2], pid0[2], len0[2];
-    bool valid[2];
+    uint4 ev[EPL];
+    uint32_t st[EPL], o0[EPL], k[EPL], pid0[EPL], len0[EPL], incl[EPL];
+    bool valid[EPL];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < EPL; ++h) {
         const uint32_t i = 32u * h + lane;
         valid[h] = i < n;
         ev[h] = valid[h] ? q[i] : make_uint4(0, 0, 0xffffffffu, 0);
         st[h] = ev[h].z;
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h)  // state after the first base of a pair: one delta lookup
+    for (int h = 0; h < EPL; ++h)  // state after the first base of a pair: one delta lookup
         if (valid[h] && (st[h] & EV_MID))
             st[h] = __ldg(tb.delta + (((st[h] & EV_STATE) << 2) | ((st[h] >> EV_BASE_SHIFT) & 3u))) & AC_STATE_MASK;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < EPL; ++h) {
         o0[h] = valid[h] ? __ldg(tb.out_off + st[h]) : 0u;
         k[h] = valid[h] ? __ldg(tb.out_off + st[h] + 1) - o0[h] : 0u;
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {  // first keyword of each set: loads in flight with the atomic
+    for (int h = 0; h < EPL; ++h) {  // first keyword of each set: loads in flight with the atomic
         pid0[h] = k[h] ? __ldg(tb.out_pid + o0[h]) : 0u;
         len0[h] = k[h] ? __ldg(tb.out_len + o0[h]) : 0u;
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < EPL; ++h) {
         const uint32_t peers = __match_any_sync(FULL, st[h]);
         if (valid[h] && lane == (uint32_t)(__ffs(peers) - 1))
             atomicAdd(&sk.hits[st[h]], (unsigned long long)__popc(peers));
     }
-    const uint32_t incl0 = warp_inclusive_sum(k[0], lane);
-    const uint32_t tot0 = __shfl_sync(FULL, incl0, 31);
-    const uint32_t incl1 = warp_inclusive_sum(k[1], lane) + tot0;
-    const uint32_t total = __shfl_sync(FULL, incl1, 31);
+    uint32_t total = 0;
+#pragma unroll
+    for (int h = 0; h < EPL; ++h) {  // exclusive offsets of every event's occurrences
+        const uint32_t in = warp_inclusive_sum(k[h], lane);
+        incl[h] = in + total;
+        total += __shfl_sync(FULL, in, 31);
+    }
     unsigned long long base = 0;
     if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
     base = __shfl_sync(FULL, base, 31);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        unsigned long long w = base + ((h ? incl1 : incl0) - k[h]);
+    for (int h = 0; h < EPL; ++h) {
+        unsigned long long w = base + (incl[h] - k[h]);
         const uint64_t end_pos = ((uint64_t)ev[h].y << 32) | ev[h].x;
         for (uint32_t t = 0; t < k[h]; ++t, ++w) {
             if (w >= sk.capacity) break;
             const uint32_t pid = t ? __ldg(tb.out_pid + o0[h] + t) : pid0[h];
-            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0[h] + t) : len0[h]);
+            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0[h] + t) : len0[h]) + sk.pos_offset;
             // streaming store: occurrences are written once and must not evict table rows from L2
             __stcs(reinterpret_cast<uint4*>(sk.matches + w),
                    make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev[h].w));
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits, a.pos_offset};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -434,6 +439,27 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint3
         }
         packed[w] = word;
         if (first_bad != ~0ull) atomicMin(bad, (unsigned long long)first_bad);
+    }
+}
+
+// Copies n bases of a packed text from base src_off of src to base dst_off
+// of dst (any offsets). One thread per destination word: it rewrites only
+// the bases of the range and keeps the other bases of its word.
+__global__ void splice_kernel(uint32_t* __restrict__ dst, uint64_t dst_off, const uint32_t* __restrict__ src,
+                              uint64_t src_off, uint64_t n) {
+    const uint64_t w0 = dst_off >> 4, w1 = (dst_off + n + 15) >> 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = w0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+        uint32_t word = dst[w];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint64_t p = (w << 4) + j;
+            if (p < dst_off || p >= dst_off + n) continue;
+            const uint64_t q = src_off + (p - dst_off);
+            const uint32_t b = (__ldg(src + (q >> 4)) >> (2 * (q & 15))) & 3u;
+            word = (word & ~(3u << (2 * j))) | (b << (2 * j));
+        }
+        dst[w] = word;
     }
 }
 
@@ -640,6 +666,18 @@ int ac_prepare_batch(const ScanShape& sh) {
     BatchArgs dummy{};
     const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{dummy, sh, nullptr, true});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
+}
+
+int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
+                     void* stream) {
+    if (n == 0) return 0;
+    const uint64_t words = ((dst_off + n + 15) >> 4) - (dst_off >> 4);
+    const DeviceProps& p = ac_device_props();
+    uint64_t blocks = (words + 255) / 256;
+    const uint64_t cap = (uint64_t)p.sms * 8;
+    if (blocks > cap) blocks = cap;
+    splice_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(dst, dst_off, src, src_off, n);
+    return (int)cudaGetLastError();
 }
 
 int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,

@@ -105,6 +105,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     a.capacity = r->capacity;
     a.counter = ctr;
     a.hits = hits;
+    a.pos_offset = 0;
     if (ac_launch_scan(a, sh, stream) != 0) return AC_ERR_CUDA;
     if (r->counts) {
         if (cudaMemsetAsync(r->counts, 0, (size_t)h.n_patterns * 8, st) != cudaSuccess) return AC_ERR_CUDA;
