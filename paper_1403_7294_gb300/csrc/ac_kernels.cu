@@ -110,7 +110,7 @@ struct Sink {
 // A hit at the first base of a two-base step is queued as the state before
 // the step plus that base (EV_MID set); the drain resolves it with one
 // delta lookup, so the walk itself never waits for it.
-constexpr int QCAP = 128;     // events per warp queue
+constexpr int QCAP = 64;  // events per warp queue (larger queues make ptxas spill the walk)
 constexpr int EPL = QCAP / 32;  // events each lane expands in drain()
 static_assert(QCAP % 32 == 0, "whole events per lane");
 constexpr uint32_t EV_MID = 0x80000000u;
