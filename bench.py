@@ -530,6 +530,56 @@ def run_serving(args, seconds: float, warm_s: float):
     }
 
 
+# ------------------------------------------ pattern-file split comparison
+
+
+def run_partition(args, steps: int = 3) -> dict:
+    """The paper's approach 2 (one machine per chunk of the keyword list, every
+    machine scanning the whole text; here each machine sized for shared
+    memory) against the single autotuned machine, on the 256 Mbase Markov
+    chromosome, for keyword sets of 1,000 .. 100,000 (length 12-30)."""
+    import ctypes
+
+    import paper_1403_7294_gb300 as acg
+    from paper_1403_7294_gb300 import _native as N
+    from paper_1403_7294_gb300 import synth
+
+    lib = acg.lib()
+    sp = torch.cuda.current_stream().cuda_stream
+    w = synth.plain_chromosome(device="cuda")
+    n = int(w.text.ascii.numel())
+    packed = acg.pack(w.text.ascii)
+    sets = synth.serve_sets(w.text.ascii, sizes=[1000, 3728, 13895, 51795, 100000])
+    desc = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
+    out = []
+    for pats in sets:
+        d = acg.build(pats)
+        acg.autotune(d, packed, n)
+        ps = acg.build_partitioned(pats)
+        row = {"patterns": len(pats), "states": d.info["n_states"], "parts": ps.n_parts,
+               "part_max_states": ps.max_states}
+        for name, fn, h in (("single", lib.ac_scan, d.h), ("partitioned", lib.ac_scan_partitioned, ps.h)):
+            r0 = N.Result(None, 0, 0, None, 1, 0, 0)
+            o = N.ScanOpts()
+            o.hot_states = -1
+            fn(h, ctypes.byref(desc), ctypes.byref(r0), ctypes.byref(o), sp, None)
+            cap = int(r0.n_matches) + 16
+            raw = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
+            r = N.Result(raw.data_ptr(), cap, 0, None, 1, 0, 0)
+            st = N.ScanStats()
+            ms = []
+            for _ in range(steps + 1):
+                assert fn(h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(o), sp, ctypes.byref(st)) == 0
+                ms.append(st.scan_ms)
+            t = float(np.median(ms[1:]))
+            row[name] = {"kernel_ms": round(t, 4), "gbases_s": round(n / t / 1e6, 2), "occurrences": int(r.n_matches)}
+        assert row["single"]["occurrences"] == row["partitioned"]["occurrences"]
+        out.append(row)
+        ps.close()
+        d.close()
+    return {"workload": f"partition-{n}b-markov", "rows": out}
+
+
 # ------------------------------------------------------- reference arm
 
 
@@ -589,7 +639,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["genome", "chromosome", "small", "batch", "serve"], default="genome")
+    ap.add_argument("--workload", choices=["genome", "chromosome", "small", "batch", "serve", "partition"],
+                    default="genome")
     ap.add_argument("--n-bases", type=int, default=None)
     ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
     ap.add_argument("--serve-seconds", type=float, default=None)
@@ -615,6 +666,15 @@ def main():
                     "ms_per_step": b["graph_replay_ms"], "higher_is_better": True, "scaling": "weak",
                     "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": {"workload": b["workload"]},
                     "batched": b})
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "partition":
+        pt = run_partition(args)
+        best = max(r["single"]["gbases_s"] for r in pt["rows"])
+        out = {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+               "data": "synthetic", "config": {"workload": pt["workload"]}, "partition": pt}
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

@@ -294,6 +294,33 @@ int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_
 int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,
                     void* stream);
 
+/* --------------------------------------------------- partitioned keyword sets
+ * The paper's own decomposition (Sec. IV.A, approach 2, Fig. 3): the keyword
+ * list is cut into consecutive chunks, one machine is built per chunk, and
+ * every machine scans the whole text; the union of their occurrences (ids
+ * offset by the chunk's first keyword) is the single machine's result. Here
+ * each chunk is sized so that its whole transition table fits in one block's
+ * shared memory, and one launch runs all machines (one grid row each). */
+
+typedef struct ac_part_set ac_part_set;
+
+/* Arguments as ac_build. max_states: the most states one machine may have;
+ * 0 = as many as one block can hold in shared memory on the current device.
+ * Chunks are consecutive keyword ranges, closed greedily when the next
+ * keyword would push the chunk's trie past max_states. Errors as ac_build;
+ * AC_ERR_TOO_LARGE when one keyword alone needs more than max_states states. */
+int ac_build_partitioned(const char* const* patterns, const uint32_t* lens, uint32_t n_patterns,
+                         uint32_t max_states, const ac_build_opts* opts /* nullable */, ac_part_set** out);
+/* Number of machines and the largest machine's state count. */
+int ac_part_set_info(const ac_part_set* set, uint32_t* n_parts, uint32_t* max_states);
+/* Scans one text with every machine of the set; semantics, buffers and
+ * errors as ac_scan (pattern ids in the caller's numbering, counts summed
+ * over machines). opts: range_begin/range_end, flags and text_id are used;
+ * the launch shape is fixed (one machine per grid row, 1024 threads). */
+int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, ac_result* result,
+                        const ac_scan_opts* opts /* nullable */, void* stream, ac_scan_stats* stats /* nullable */);
+void ac_part_set_free(ac_part_set* set);
+
 /* ---------------------------------------------------------- streaming scans
  * One long text delivered in consecutive pieces (for example read from a
  * file block by block: the paper's module reads both the keywords and the

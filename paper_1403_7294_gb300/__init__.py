@@ -23,7 +23,8 @@ from . import _native as N
 from ._native import AcError
 
 __all__ = [
-    "Dfa", "ScanResult", "build", "pack", "scan", "scan_batch", "BatchPlan", "Stream", "autotune", "Server",
+    "Dfa", "ScanResult", "build", "pack", "scan", "scan_batch", "BatchPlan", "Stream", "PartSet",
+    "build_partitioned", "autotune", "Server",
     "AcError", "lib",
 ]
 
@@ -308,6 +309,57 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class PartSet:
+    """The paper's pattern-file split (Sec. IV.A, approach 2): one machine per
+    consecutive chunk of keywords, each small enough for shared memory, all
+    scanning the whole text in one launch (ac_build_partitioned /
+    ac_scan_partitioned). Ids and counts are in the caller's numbering."""
+
+    def __init__(self, patterns: Sequence, max_states: int = 0, fold_case: bool = False):
+        bufs = [_as_bytes(p) for p in patterns]
+        n = len(bufs)
+        ptrs = (ctypes.c_char_p * max(n, 1))(*bufs)
+        lens = np.array([len(b) for b in bufs], dtype=np.uint32)
+        opts = N.BuildOpts(N.AC_BUILD_FOLD_CASE if fold_case else 0, 0)
+        h = ctypes.c_void_p()
+        N.check(lib().ac_build_partitioned(ctypes.cast(ptrs, ctypes.c_void_p), lens.ctypes.data, n, max_states,
+                                           ctypes.byref(opts), ctypes.byref(h)), "ac_build_partitioned")
+        self.h = h
+        self.n_patterns = n
+        k, m = ctypes.c_uint32(), ctypes.c_uint32()
+        N.check(lib().ac_part_set_info(self.h, ctypes.byref(k), ctypes.byref(m)), "ac_part_set_info")
+        self.n_parts, self.max_states = k.value, m.value
+
+    def scan(self, text, *, encoding: int | None = None, n_bases: int | None = None, capacity: int | None = None,
+             counts: bool = True, range_=None, fold_case: bool = False, stats: bool = False, stream=None,
+             results_on_device: bool | None = None) -> ScanResult:
+        desc, keep = _text_desc(text, encoding, n_bases)
+        on_dev = bool(desc.on_device) if results_on_device is None else results_on_device
+        device = text.device if isinstance(text, torch.Tensor) and text.is_cuda else torch.device("cuda")
+        if capacity is None:
+            capacity = max(1024, desc.n_bases // 64)
+        o = _opts(range_, 0, 0, 0, -1, fold_case)
+        res = _run(lib().ac_scan_partitioned, self, ctypes.byref(desc), None, capacity, counts, device, o,
+                   _stream_ptr(stream), stats, on_dev, handle=self.h)
+        del keep
+        return res
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ac_part_set_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_partitioned(patterns: Sequence, max_states: int = 0, fold_case: bool = False) -> PartSet:
+    return PartSet(patterns, max_states=max_states, fold_case=fold_case)
 
 
 class Stream:

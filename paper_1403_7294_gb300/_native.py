@@ -115,6 +115,11 @@ SIGNATURES = {
     "ac_scan_noalloc": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P]),
     "ac_scan_batch": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
                                      ctypes.POINTER(ScanOpts), P, ctypes.POINTER(ScanStats)]),
+    "ac_build_partitioned": (ctypes.c_int, [P, P, u32, u32, P, ctypes.POINTER(P)]),
+    "ac_part_set_info": (ctypes.c_int, [P, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
+    "ac_scan_partitioned": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,
+                                           ctypes.POINTER(ScanStats)]),
+    "ac_part_set_free": (None, [P]),
     "ac_stream_create": (ctypes.c_int, [P, ctypes.POINTER(P)]),
     "ac_stream_scan": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,
                                       ctypes.POINTER(ScanStats)]),

@@ -599,11 +599,223 @@ extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, 
     // on any error (overflow included) the stream is unchanged and the piece can
     // be sent again (an alphabet error's bad_offset is relative to the piece)
     if (status != AC_OK) return status;
-    // the last L_max - 1 bases become the carry of the next piece
+    // the last L_max - 1 bases become the carry of the next piece (keep <= carry_cap)
     const uint64_t keep = std::min<uint64_t>(total, h.max_len ? h.max_len - 1 : 0);
     if ((rc = ac_launch_splice(s->d_carry, 0, comb, total - keep, keep, st)) != 0) return cuda_status((cudaError_t)rc);
     s->carry_n = keep;
     s->consumed += n;
+    return status;
+}
+
+// ------------------------------------------------- partitioned keyword sets
+
+namespace {
+// 2-bit code of a base in either case (other bytes map to 0 here; ac_build rejects them)
+inline int sym2(uint8_t c) { return ((c >> 1) ^ (c >> 2)) & 3; }
+}  // namespace
+
+struct ac_part_set {
+    std::vector<ac_dfa*> parts;
+    std::vector<uint32_t> first_pid;  // first keyword id of each chunk
+    uint32_t n_patterns = 0;
+    uint32_t max_states = 0;
+    uint32_t halo = 0;
+    uint64_t total_states = 0;
+};
+
+extern "C" void ac_part_set_free(ac_part_set* s) {
+    if (!s) return;
+    for (ac_dfa* d : s->parts) ac_free(d);
+    delete s;
+}
+
+extern "C" int ac_build_partitioned(const char* const* patterns, const uint32_t* lens, uint32_t n, uint32_t max_states,
+                                    const ac_build_opts* opts, ac_part_set** out) {
+    if (!patterns || !lens || n == 0 || !out) return AC_ERR_INVALID_ARG;
+    const uint32_t cap = max_states ? max_states : ac_max_hot_states(ac_max_threads(1), 1);
+    if (cap < 2) return AC_ERR_INVALID_ARG;
+    // Chunk boundaries: insert keywords into a trie, counting its states, and
+    // close the chunk before a keyword that would take it past `cap`.
+    std::vector<uint32_t> bounds{0};
+    try {
+        std::vector<int32_t> child(4, -1);
+        uint32_t nodes = 1;
+        for (uint32_t p = 0; p < n; ++p) {
+            if (!patterns[p] || lens[p] == 0) return lens[p] == 0 ? AC_ERR_EMPTY_PATTERN : AC_ERR_INVALID_ARG;
+            if ((uint64_t)lens[p] + 1 > cap) return AC_ERR_TOO_LARGE;
+            for (int pass = 0; pass < 2; ++pass) {
+                // new states this keyword adds (bytes outside ACGT are left to ac_build to reject)
+                uint32_t s = 0, j = 0;
+                for (; j < lens[p]; ++j) {
+                    const int c = sym2((uint8_t)patterns[p][j]);
+                    const int32_t t = child[(size_t)s * 4 + c];
+                    if (t < 0) break;
+                    s = (uint32_t)t;
+                }
+                if (nodes + (lens[p] - j) <= cap) {
+                    for (; j < lens[p]; ++j) {
+                        const int c = sym2((uint8_t)patterns[p][j]);
+                        child[(size_t)s * 4 + c] = (int32_t)nodes;
+                        child.insert(child.end(), {-1, -1, -1, -1});
+                        s = nodes++;
+                    }
+                    break;
+                }
+                // close the chunk and start a new trie with this keyword
+                bounds.push_back(p);
+                child.assign(4, -1);
+                nodes = 1;
+            }
+        }
+        bounds.push_back(n);
+    } catch (const std::bad_alloc&) {
+        return AC_ERR_OOM;
+    }
+    ac_part_set* s = new (std::nothrow) ac_part_set();
+    if (!s) return AC_ERR_OOM;
+    s->n_patterns = n;
+    ac_build_opts o{};
+    o.flags = (opts ? opts->flags : 0u) | AC_BUILD_NO_STRIDE2;
+    for (size_t i = 0; i + 1 < bounds.size(); ++i) {
+        const uint32_t a = bounds[i], b = bounds[i + 1];
+        if (a == b) continue;
+        ac_dfa* d = nullptr;
+        const int rc = ac_build(patterns + a, lens + a, b - a, &o, &d);
+        if (rc != AC_OK) {
+            ac_part_set_free(s);
+            return rc;
+        }
+        if (d->host.n_states > cap) {  // cannot happen with the trie count above; keep the invariant checked
+            ac_free(d);
+            ac_part_set_free(s);
+            return AC_ERR_TOO_LARGE;
+        }
+        s->parts.push_back(d);
+        s->first_pid.push_back(a);
+        s->max_states = std::max(s->max_states, d->host.n_states);
+        s->halo = std::max(s->halo, d->host.max_len - 1);
+        s->total_states += d->host.n_states;
+    }
+    *out = s;
+    return AC_OK;
+}
+
+extern "C" int ac_part_set_info(const ac_part_set* s, uint32_t* n_parts, uint32_t* max_states) {
+    if (!s) return AC_ERR_INVALID_ARG;
+    if (n_parts) *n_parts = (uint32_t)s->parts.size();
+    if (max_states) *max_states = s->max_states;
+    return AC_OK;
+}
+
+extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, ac_result* r,
+                                   const ac_scan_opts* opts, void* stream, ac_scan_stats* stats) {
+    if (!set || !text || !r) return AC_ERR_INVALID_ARG;
+    r->bad_offset = ~0ull;
+    if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
+        return AC_ERR_INVALID_ARG;
+    const uint64_t n = text->n_bases;
+    const uint64_t own_begin = opts ? opts->range_begin : 0;
+    const uint64_t own_end = (opts && opts->range_end) ? opts->range_end : n;
+    if (own_begin > own_end || own_end > n) return AC_ERR_INVALID_ARG;
+    const uint32_t k = (uint32_t)set->parts.size();
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    Events ev(stats != nullptr, st);
+    Scratch sc(st);
+    cudaError_t e;
+    ev.rec(0);
+    unsigned long long* d_ctr = nullptr;
+    unsigned long long* d_hits = nullptr;
+    PartDesc* d_parts = nullptr;
+    if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, std::max<uint64_t>(set->total_states, 1) * 8)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = sc.get((void**)&d_parts, std::max<size_t>(k, 1) * sizeof(PartDesc))) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, set->total_states * 8, st)) != cudaSuccess) return cuda_status(e);
+    std::vector<PartDesc> pd(k);
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+        const ac_dfa* d = set->parts[i];
+        pd[i] = PartDesc{d->d_delta, d->d_out_off, d->d_out_pid, d->d_out_len, d_hits + off, d->host.n_states,
+                         set->first_pid[i]};
+        off += d->host.n_states;
+    }
+    if (k && (e = cudaMemcpyAsync(d_parts, pd.data(), k * sizeof(PartDesc), cudaMemcpyHostToDevice, st)) !=
+                 cudaSuccess)
+        return cuda_status(e);
+    ev.rec(1);
+    const uint32_t* words = nullptr;
+    int rc = stage_packed(text, fold, st, sc, d_ctr + 2, &words);
+    if (rc != AC_OK) return rc;
+    ev.rec(2);
+    ac_match* d_matches = r->matches;
+    unsigned long long* d_counts = (unsigned long long*)r->counts;
+    if (!r->on_device) {
+        if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
+        if (r->counts && (e = sc.get((void**)&d_counts, (size_t)set->n_patterns * 8)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    // one grid row per machine; the rows share the SMs
+    const DeviceProps& p = ac_device_props();
+    const uint32_t threads = ac_max_threads(1);
+    const uint32_t gx = std::max<uint32_t>(1, (uint32_t)p.sms / std::max<uint32_t>(k, 1));
+    const uint64_t owned = own_end - own_begin;
+    const uint32_t chunk = (uint32_t)std::min<uint64_t>(
+        std::max<uint64_t>((owned + (uint64_t)gx * threads - 1) / ((uint64_t)gx * threads),
+                           std::max<uint64_t>(64, round_up(set->halo, 64))),
+        1u << 30);
+    PartArgs a;
+    a.parts = d_parts;
+    a.text = words;
+    a.n = n;
+    a.own_begin = own_begin;
+    a.own_end = own_end;
+    a.halo = set->halo;
+    a.max_states = set->max_states;
+    a.matches = d_matches;
+    a.capacity = r->capacity;
+    a.counter = d_ctr;
+    ev.rec(3);
+    rc = ac_launch_part_scan(a, k, gx, threads, chunk, st);
+    if (rc) return cuda_status((cudaError_t)rc);
+    ev.rec(4);
+    if (d_counts) {
+        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)set->n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
+        for (uint32_t i = 0; i < k; ++i) {
+            const ac_dfa* d = set->parts[i];
+            rc = ac_launch_counts(d->d_out_off, d->d_out_pid, d->host.n_states, pd[i].hits, d_counts + set->first_pid[i],
+                                  st);
+            if (rc) return cuda_status((cudaError_t)rc);
+        }
+    }
+    ev.rec(5);
+    const int status =
+        finish(st, d_ctr, text->encoding == AC_TEXT_ASCII ? d_ctr + 2 : nullptr, r, d_matches, d_counts, set->n_patterns);
+    ev.rec(6);
+    if (stats) {
+        cudaEventSynchronize(ev.ev[6]);
+        stats->total_ms = ev.ms(0, 6);
+        stats->pack_ms = ev.ms(1, 2);
+        stats->scan_ms = ev.ms(3, 4);
+        stats->counts_ms = ev.ms(4, 5);
+        stats->chunk = chunk;
+        stats->threads = threads;
+        stats->interleave = 1;
+        stats->hot_states = set->max_states;
+        stats->grid = gx * k;
+        stats->blocks_per_sm = 1;
+        stats->stride = 1;
+        const uint64_t n_chunks = owned ? (owned + chunk - 1) / chunk : 0;
+        stats->bases_walked = (uint64_t)k * (owned + n_chunks * set->halo);
+    }
     return status;
 }
 

@@ -136,6 +136,31 @@ struct BatchArgs {
     unsigned long long* hits;
 };
 int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream);
+
+// Partitioned keyword sets (ac_kernels.cu): one machine per chunk of keywords.
+struct PartDesc {
+    const uint32_t* delta;     // [S*4], all rows staged in shared memory
+    const uint32_t* out_off;
+    const uint32_t* out_pid;   // local ids
+    const uint32_t* out_len;
+    unsigned long long* hits;  // [S] slice of the shared hit buffer
+    uint32_t n_states;
+    uint32_t pid_offset;       // first keyword id of the chunk
+};
+struct PartArgs {
+    const PartDesc* parts;     // [n_parts] device
+    const uint32_t* text;
+    uint64_t n;
+    uint64_t own_begin, own_end;
+    uint32_t halo;             // longest keyword of all chunks - 1
+    uint32_t max_states;       // largest machine (shared-memory rows)
+    ac_match* matches;
+    uint64_t capacity;
+    unsigned long long* counter;
+};
+// Launches grid (grid_x, n_parts) x threads, interleave 1.
+int ac_launch_part_scan(const PartArgs& a, uint32_t n_parts, uint32_t grid_x, uint32_t threads, uint32_t chunk,
+                        void* stream);
 // Sets the batch kernel's shared-memory limit for a shape (call before graph capture).
 int ac_prepare_batch(const ScanShape& sh);
 

@@ -101,6 +101,7 @@ struct Sink {
     unsigned long long* counter;
     unsigned long long* hits;
     uint64_t pos_offset;  // added to every reported start (streaming scans)
+    uint32_t pid_offset;  // added to every reported keyword id (partitioned keyword sets)
 };
 
 // Hits wait in a per-warp queue in shared memory, 16 B per event:
@@ -187,7 +188,7 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
         const uint64_t end_pos = ((uint64_t)ev[h].y << 32) | ev[h].x;
         for (uint32_t t = 0; t < k[h]; ++t, ++w) {
             if (w >= sk.capacity) break;
-            const uint32_t pid = t ? __ldg(tb.out_pid + o0[h] + t) : pid0[h];
+            const uint32_t pid = (t ? __ldg(tb.out_pid + o0[h] + t) : pid0[h]) + sk.pid_offset;
             const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0[h] + t) : len0[h]) + sk.pos_offset;
             // streaming store: occurrences are written once and must not evict table rows from L2
             __stcs(reinterpret_cast<uint4*>(sk.matches + w),
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits, a.pos_offset};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits, a.pos_offset, 0u};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
     const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -404,6 +405,41 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
             }
         }
         walk<I, ST>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
+    }
+}
+
+// The paper's approach 2 (Sec. IV.A, Fig. 3): the keyword list is cut into
+// consecutive chunks and each chunk gets its own machine; every machine scans
+// the whole text. blockIdx.y selects the machine; each machine is small
+// enough to live entirely in shared memory, and its keyword ids are offset
+// back into the caller's numbering.
+template <int I>
+__global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArgs a, uint32_t chunk, uint64_t n_chunks) {
+    extern __shared__ uint4 sm_rows[];
+    const PartDesc pd = a.parts[blockIdx.y];
+    stage_hot(sm_rows, pd.delta, pd.n_states);
+    const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
+    const uint64_t pol_tab = policy_evict_last();
+    const uint64_t pol_txt = policy_evict_first();
+    const Tables tb{pd.delta, nullptr, 0u, pd.out_off, pd.out_pid, pd.out_len};
+    const Sink sk{a.matches, a.capacity, a.counter, pd.hits, 0ull, pd.pid_offset};
+    uint4* q = sm_rows + a.max_states + (threadIdx.x >> 5) * QCAP;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nwords = (a.n + 15) >> 4;
+    for (uint64_t round = 0; round < n_chunks; round += T * I) {
+        Chain ch[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const uint64_t c = round + (uint64_t)j * T + t;
+            if (c < n_chunks) {
+                const uint64_t lo = a.own_begin + c * chunk;
+                set_chain(ch[j], a.text, nwords, 0u, lo, min(lo + chunk, a.own_end), a.halo);
+            } else {
+                idle_chain(ch[j], a.text, nwords, 0u);
+            }
+        }
+        walk<I, 1>(ch, sm, pd.n_states, tb, sk, q, pol_tab, pol_txt);
     }
 }
 
@@ -666,6 +702,18 @@ int ac_prepare_batch(const ScanShape& sh) {
     BatchArgs dummy{};
     const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{dummy, sh, nullptr, true});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
+}
+
+int ac_launch_part_scan(const PartArgs& a, uint32_t n_parts, uint32_t grid_x, uint32_t threads, uint32_t chunk,
+                        void* stream) {
+    const uint64_t owned = a.own_end > a.own_begin ? a.own_end - a.own_begin : 0;
+    if (owned == 0 || n_parts == 0) return 0;
+    const uint64_t n_chunks = (owned + chunk - 1) / chunk;
+    const size_t smem = ac_scan_smem_bytes(a.max_states, threads, 1);
+    int rc = set_smem(part_scan_kernel<1>, smem);
+    if (rc) return rc;
+    part_scan_kernel<1><<<dim3(grid_x, n_parts), threads, smem, (cudaStream_t)stream>>>(a, chunk, n_chunks);
+    return (int)cudaGetLastError();
 }
 
 int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
