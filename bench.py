@@ -177,6 +177,12 @@ def run_plain(args, world, rank, local):
     t0 = time.time()
     w = make_workload(args.workload, args.n_bases, "cuda", rank)
     n = int(w.text.ascii.numel())
+    if args.uniform_patterns:  # the walk-only case: keywords of the same shape that never occur
+        from paper_1403_7294_gb300 import synth
+
+        lo, hi = {"genome": (20, 25), "chromosome": (18, 30), "small": (8, 20)}[args.workload]
+        w.patterns = synth.uniform_patterns(len(w.patterns), lo, hi, synth.BASE_SEED + 77)
+        w.name += "-uniform-keywords"
     log(f"[bench] workload {w.name}: generated in {time.time() - t0:.1f}s")
     t0 = time.time()
     dfa = acg.build(w.patterns)
@@ -644,6 +650,8 @@ def main():
     ap.add_argument("--n-bases", type=int, default=None)
     ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
     ap.add_argument("--serve-seconds", type=float, default=None)
+    ap.add_argument("--uniform-patterns", action="store_true",
+                    help="replace the keywords by uniform random ones of the same shape (walk-only ceiling)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.minimal:
         log("[bench] warmup raised to 3")

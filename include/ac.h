@@ -71,8 +71,10 @@ enum ac_build_flags {
     AC_BUILD_FOLD_CASE = 1u, /* accept a,c,g,t in keywords as A,C,G,T                          */
     AC_BUILD_HOST_ONLY = 2u, /* build the tables on the host only (no GPU needed); such a dfa
                                 can be inspected with ac_dfa_tables but not scanned          */
-    AC_BUILD_NO_STRIDE2 = 4u /* skip the two-bases-per-lookup table (saves 64 B per state of
+    AC_BUILD_NO_STRIDE2 = 4u, /* skip the two-bases-per-lookup table (saves 64 B per state of
                                 device memory; scans then always read one base per lookup)   */
+    AC_BUILD_FAILURELESS = 8u /* also keep the trie edges and per-state own keywords, for
+                                ac_scan_failureless (16 B per state + 8 B per keyword)        */
 };
 
 typedef struct {
@@ -143,6 +145,13 @@ typedef struct {
     const uint32_t* depth;
     const uint32_t* fail;
     const uint32_t* delta2;
+    /* failure-less form (NULL unless built with AC_BUILD_FAILURELESS):
+     * gotos[4*s + c] = trie child (bit 31 set when keywords end there) or
+     * 0x7fffffff where s has no c edge; own_off[S+1], own_pid[P]: the keywords
+     * ending exactly at each state */
+    const uint32_t* gotos;
+    const uint32_t* own_off;
+    const uint32_t* own_pid;
 } ac_dfa_tables_t;
 
 int ac_dfa_tables(const ac_dfa* dfa, ac_dfa_tables_t* out);
@@ -293,6 +302,18 @@ int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_
 
 int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,
                     void* stream);
+
+/* ----------------------------------------------------- failure-less matching
+ * The failure-less scheme the paper cites among related work (Sec. II, the
+ * PFAC algorithm): one GPU thread per start position walks only the trie's
+ * goto edges from the root, stops at the first missing edge, and reports the
+ * keywords ending at each state it passes. Every occurrence is found by the
+ * thread of its own start, so failure transitions are not needed. Same
+ * results, buffers and errors as ac_scan (ownership by end position); needs a
+ * dfa built with AC_BUILD_FAILURELESS, else AC_ERR_INVALID_ARG. Provided for
+ * comparison with the failure-folded walk of ac_scan. */
+int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_result* result,
+                        const ac_scan_opts* opts /* nullable */, void* stream, ac_scan_stats* stats /* nullable */);
 
 /* --------------------------------------------------- partitioned keyword sets
  * The paper's own decomposition (Sec. IV.A, approach 2, Fig. 3): the keyword

@@ -23,7 +23,7 @@ from . import _native as N
 from ._native import AcError
 
 __all__ = [
-    "Dfa", "ScanResult", "build", "pack", "scan", "scan_batch", "BatchPlan", "Stream", "PartSet",
+    "Dfa", "ScanResult", "build", "pack", "scan", "scan_failureless", "scan_batch", "BatchPlan", "Stream", "PartSet",
     "build_partitioned", "autotune", "Server",
     "AcError", "lib",
 ]
@@ -58,14 +58,15 @@ class Dfa:
     """A built machine (ac_build). Immutable; freed with close() or on GC."""
 
     def __init__(self, patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True,
-                 stride2_states: int = 0):
+                 stride2_states: int = 0, failureless: bool = False):
         L = lib()
         self._bufs = [_as_bytes(p) for p in patterns]
         n = len(self._bufs)
         ptrs = (ctypes.c_char_p * max(n, 1))(*self._bufs)
         lens = np.array([len(b) for b in self._bufs], dtype=np.uint32)
         opts = N.BuildOpts((N.AC_BUILD_FOLD_CASE if fold_case else 0) | (N.AC_BUILD_HOST_ONLY if host_only else 0)
-                           | (0 if stride2 else N.AC_BUILD_NO_STRIDE2), stride2_states)
+                           | (0 if stride2 else N.AC_BUILD_NO_STRIDE2) | (N.AC_BUILD_FAILURELESS if failureless else 0),
+                           stride2_states)
         h = ctypes.c_void_p()
         N.check(L.ac_build(ctypes.cast(ptrs, ctypes.c_void_p), lens.ctypes.data, n, ctypes.byref(opts),
                            ctypes.byref(h)), "ac_build")
@@ -91,6 +92,8 @@ class Dfa:
         S, Pn, E = self.info["n_states"], self.info["n_patterns"], self.info["out_entries"]
         sizes = {"delta": 4 * S, "out_off": S + 1, "out_pid": E, "pat_len": Pn, "pat_state": Pn, "depth": S, "fail": S,
                  "delta2": self.info["table2_bytes"] // 4}
+        if t.gotos:  # failure-less form
+            sizes.update({"gotos": 4 * S, "own_off": S + 1, "own_pid": Pn})
         return {k: np.ctypeslib.as_array(getattr(t, k), shape=(v,)).copy() if v else np.zeros(0, np.uint32)
                 for k, v in sizes.items()}
 
@@ -107,8 +110,9 @@ class Dfa:
 
 
 def build(patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True,
-          stride2_states: int = 0) -> Dfa:
-    return Dfa(patterns, fold_case=fold_case, host_only=host_only, stride2=stride2, stride2_states=stride2_states)
+          stride2_states: int = 0, failureless: bool = False) -> Dfa:
+    return Dfa(patterns, fold_case=fold_case, host_only=host_only, stride2=stride2, stride2_states=stride2_states,
+               failureless=failureless)
 
 
 # ------------------------------------------------------------------- texts
@@ -236,6 +240,24 @@ def scan(dfa: Dfa, text, *, encoding: int | None = None, n_bases: int | None = N
     o = _opts(range_, chunk, threads, interleave, hot_states, fold_case, text_id, stride)
     res = _run(lib().ac_scan, dfa, ctypes.byref(desc), None, capacity, counts, device, o, _stream_ptr(stream),
                stats, on_dev)
+    del keep
+    return res
+
+
+def scan_failureless(dfa: Dfa, text, *, encoding: int | None = None, n_bases: int | None = None,
+                     capacity: int | None = None, counts: bool = True, range_=None, fold_case: bool = False,
+                     text_id: int = 0, stats: bool = False, stream=None,
+                     results_on_device: bool | None = None) -> ScanResult:
+    """Failure-less matching, one thread per start position (ac_scan_failureless);
+    the dfa must be built with failureless=True."""
+    desc, keep = _text_desc(text, encoding, n_bases)
+    on_dev = bool(desc.on_device) if results_on_device is None else results_on_device
+    device = text.device if isinstance(text, torch.Tensor) and text.is_cuda else torch.device("cuda")
+    if capacity is None:
+        capacity = max(1024, desc.n_bases // 64)
+    o = _opts(range_, 0, 0, 0, -1, fold_case, text_id)
+    res = _run(lib().ac_scan_failureless, dfa, ctypes.byref(desc), None, capacity, counts, device, o,
+               _stream_ptr(stream), stats, on_dev)
     del keep
     return res
 

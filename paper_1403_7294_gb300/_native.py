@@ -28,6 +28,7 @@ AC_ERR_NO_DEVICE = -11
 AC_BUILD_FOLD_CASE = 1
 AC_BUILD_HOST_ONLY = 2
 AC_BUILD_NO_STRIDE2 = 4
+AC_BUILD_FAILURELESS = 8
 AC_TEXT_ASCII = 0
 AC_TEXT_PACKED2 = 1
 AC_SCAN_FOLD_CASE = 1
@@ -51,7 +52,8 @@ class DfaInfo(ctypes.Structure):
 
 class DfaTables(ctypes.Structure):
     _fields_ = [(k, ctypes.POINTER(u32))
-                for k in ("delta", "out_off", "out_pid", "pat_len", "pat_state", "depth", "fail", "delta2")]
+                for k in ("delta", "out_off", "out_pid", "pat_len", "pat_state", "depth", "fail", "delta2", "gotos",
+                          "own_off", "own_pid")]
 
 
 class Text(ctypes.Structure):
@@ -115,6 +117,8 @@ SIGNATURES = {
     "ac_scan_noalloc": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P]),
     "ac_scan_batch": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(Result),
                                      ctypes.POINTER(ScanOpts), P, ctypes.POINTER(ScanStats)]),
+    "ac_scan_failureless": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,
+                                           ctypes.POINTER(ScanStats)]),
     "ac_build_partitioned": (ctypes.c_int, [P, P, u32, u32, P, ctypes.POINTER(P)]),
     "ac_part_set_info": (ctypes.c_int, [P, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
     "ac_scan_partitioned": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(Result), ctypes.POINTER(ScanOpts), P,

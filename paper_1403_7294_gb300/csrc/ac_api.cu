@@ -150,8 +150,8 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
     ac_dfa* d = new (std::nothrow) ac_dfa();
     if (!d) return AC_ERR_OOM;
     int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0,
-                           (flags & AC_BUILD_NO_STRIDE2) == 0, opts ? opts->stride2_states : 0u, &d->host,
-                           nullptr);
+                           (flags & AC_BUILD_NO_STRIDE2) == 0, opts ? opts->stride2_states : 0u,
+                           (flags & AC_BUILD_FAILURELESS) != 0, &d->host, nullptr);
     if (rc != AC_OK) {
         delete d;
         return rc;
@@ -163,10 +163,13 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
             uint32_t** dst;
             const std::vector<uint32_t>* src;
         } ups[] = {{&d->d_delta, &h.delta}, {&d->d_out_off, &h.out_off}, {&d->d_out_pid, &h.out_pid},
-                   {&d->d_out_len, &h.out_len}, {&d->d_delta2, &h.delta2}};
+                   {&d->d_out_len, &h.out_len}, {&d->d_delta2, &h.delta2}, {&d->d_gotos, &h.gotos},
+                   {&d->d_own_off, &h.own_off}, {&d->d_own_pid, &h.own_pid}, {&d->d_own_len, &h.own_len}};
         cudaError_t e = cudaSuccess;
         for (auto& u : ups) {
-            if (u.dst == &d->d_delta2 && u.src->empty()) continue;  // two-base table not built
+            const bool optional = u.dst == &d->d_delta2 || u.dst == &d->d_gotos || u.dst == &d->d_own_off ||
+                                  u.dst == &d->d_own_pid || u.dst == &d->d_own_len;
+            if (optional && u.src->empty()) continue;  // two-base / failure-less tables not built
             const size_t bytes = std::max<size_t>(u.src->size(), 1) * sizeof(uint32_t);
             e = dev_alloc((void**)u.dst, bytes);
             if (e != cudaSuccess) break;
@@ -197,6 +200,10 @@ extern "C" void ac_free(ac_dfa* d) {
         cudaFree(d->d_out_off);
         cudaFree(d->d_out_pid);
         cudaFree(d->d_out_len);
+        cudaFree(d->d_gotos);
+        cudaFree(d->d_own_off);
+        cudaFree(d->d_own_pid);
+        cudaFree(d->d_own_len);
         cudaSetDevice(cur);
     }
     delete d;
@@ -230,6 +237,9 @@ extern "C" int ac_dfa_tables(const ac_dfa* d, ac_dfa_tables_t* o) {
     o->depth = h.depth.data();
     o->fail = h.fail.data();
     o->delta2 = h.delta2.empty() ? nullptr : h.delta2.data();
+    o->gotos = h.gotos.empty() ? nullptr : h.gotos.data();
+    o->own_off = h.own_off.empty() ? nullptr : h.own_off.data();
+    o->own_pid = h.own_pid.empty() ? nullptr : h.own_pid.data();
     return AC_OK;
 }
 
@@ -353,7 +363,7 @@ int finish(cudaStream_t st, const unsigned long long* d_counter, const unsigned 
 int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own_begin, uint64_t own_end,
               uint64_t pos_offset, ac_result* r, const ac_scan_opts* opts, cudaStream_t st, Scratch& sc,
               unsigned long long* d_ctr, unsigned long long* d_hits, bool check_alphabet, Events& ev,
-              ac_scan_stats* stats) {
+              ac_scan_stats* stats, bool failureless = false) {
     const HostTables& h = dfa->host;
     cudaError_t e;
     // ---- outputs
@@ -363,6 +373,53 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
         if ((e = sc.get((void**)&d_matches, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
         if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess)
             return cuda_status(e);
+    }
+    if (failureless) {  // one lane per start position over the trie edges
+        const uint32_t hot = std::min(h.n_states, ac_max_hot_states(1024, 1));
+        FlArgs f;
+        f.gotos = dfa->d_gotos;
+        f.own_off = dfa->d_own_off;
+        f.own_pid = dfa->d_own_pid;
+        f.own_len = dfa->d_own_len;
+        f.text = words;
+        f.n = n;
+        f.own_begin = own_begin;
+        f.own_end = own_end;
+        f.halo = h.max_len - 1;
+        f.text_id = opts ? opts->text_id : 0u;
+        f.matches = d_matches;
+        f.capacity = r->capacity;
+        f.counter = d_ctr;
+        f.hits = d_hits;
+        ev.rec(3);
+        int rc = ac_launch_failureless(f, hot, st);
+        if (rc) return cuda_status((cudaError_t)rc);
+        ev.rec(4);
+        if (d_counts) {
+            if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
+            rc = ac_launch_counts(dfa->d_own_off, dfa->d_own_pid, h.n_states, d_hits, d_counts, st);
+            if (rc) return cuda_status((cudaError_t)rc);
+        }
+        ev.rec(5);
+        const int status =
+            finish(st, d_ctr, check_alphabet ? d_ctr + 2 : nullptr, r, d_matches, d_counts, h.n_patterns);
+        ev.rec(6);
+        if (stats) {
+            cudaEventSynchronize(ev.ev[6]);
+            stats->total_ms = ev.ms(0, 6);
+            stats->pack_ms = ev.ms(1, 2);
+            stats->scan_ms = ev.ms(3, 4);
+            stats->counts_ms = ev.ms(4, 5);
+            stats->chunk = 1;
+            stats->threads = 1024;
+            stats->interleave = 1;
+            stats->hot_states = hot;
+            stats->grid = 0;
+            stats->blocks_per_sm = 0;
+            stats->stride = 1;
+            stats->bases_walked = own_end - own_begin;
+        }
+        return status;
     }
     // ---- the scan
     const ScanShape sh = ac_default_shape(dfa, own_end - own_begin, opts);
@@ -505,6 +562,48 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     ev.rec(2);
     return scan_core(dfa, words, n, own_begin, own_end, 0, r, opts, st, sc, d_ctr, d_hits,
                      text->encoding == AC_TEXT_ASCII, ev, stats);
+}
+
+// ------------------------------------------------------ failure-less scan
+
+extern "C" int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts,
+                                   void* stream, ac_scan_stats* stats) {
+    if (!dfa || !text || !r) return AC_ERR_INVALID_ARG;
+    r->bad_offset = ~0ull;
+    if (!dfa->on_device) return AC_ERR_NO_DEVICE;
+    if (!dfa->d_gotos) return AC_ERR_INVALID_ARG;  // built without AC_BUILD_FAILURELESS
+    if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
+    if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
+        return AC_ERR_INVALID_ARG;
+    const uint64_t n = text->n_bases;
+    const uint64_t own_begin = opts ? opts->range_begin : 0;
+    const uint64_t own_end = (opts && opts->range_end) ? opts->range_end : n;
+    if (own_begin > own_end || own_end > n) return AC_ERR_INVALID_ARG;
+    const HostTables& h = dfa->host;
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    Events ev(stats != nullptr, st);
+    Scratch sc(st);
+    cudaError_t e;
+    ev.rec(0);
+    unsigned long long* d_ctr = nullptr;
+    unsigned long long* d_hits = nullptr;
+    if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
+    ev.rec(1);
+    const uint32_t* words = nullptr;
+    const int rc = stage_packed(text, fold, st, sc, d_ctr + 2, &words);
+    if (rc != AC_OK) return rc;
+    ev.rec(2);
+    return scan_core(dfa, words, n, own_begin, own_end, 0, r, opts, st, sc, d_ctr, d_hits,
+                     text->encoding == AC_TEXT_ASCII, ev, stats, true);
 }
 
 // --------------------------------------------------------------- streaming

@@ -44,7 +44,8 @@ inline int base_code(uint8_t c, bool fold) {
 }  // namespace
 
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, uint32_t stride2_states, HostTables* t, uint32_t* bad_pattern) {
+                  bool with_stride2, uint32_t stride2_states, bool with_failureless, HostTables* t,
+                  uint32_t* bad_pattern) {
     if (!patterns || !lens || n == 0 || !t) return AC_ERR_INVALID_ARG;
     uint64_t total = 0;
     for (uint32_t p = 0; p < n; ++p) {
@@ -176,6 +177,32 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
         for (uint32_t p = 0; p < n; ++p) t->pat_state[p] = bfs_id[pat_node[p]];
         t->out_len.resize(E);
         for (uint64_t k = 0; k < E; ++k) t->out_len[k] = lens[t->out_pid[k]];
+
+        // ---- failure-less form (trie edges only): goto[s][c] = child or AC_NO_EDGE,
+        // bit 31 = the child is where some keyword ends; own keywords per state as CSR
+        t->gotos.clear();
+        t->own_off.clear();
+        t->own_pid.clear();
+        if (with_failureless) {
+            t->gotos.assign((size_t)S * 4, AC_NO_EDGE);
+            t->own_off.assign((size_t)S + 1, 0);
+            for (uint32_t p = 0; p < n; ++p) t->own_off[t->pat_state[p] + 1]++;
+            for (uint32_t i = 0; i < S; ++i) t->own_off[i + 1] += t->own_off[i];
+            t->own_pid.assign(n, 0);
+            std::vector<uint32_t> fill(t->own_off.begin(), t->own_off.end() - 1);
+            for (uint32_t p = 0; p < n; ++p) t->own_pid[fill[t->pat_state[p]]++] = p;  // ids ascending per state
+            t->own_len.resize(n);
+            for (uint32_t j = 0; j < n; ++j) t->own_len[j] = lens[t->own_pid[j]];
+            for (uint32_t i = 0; i < S; ++i) {
+                const uint32_t s = order[i];
+                for (int c = 0; c < 4; ++c) {
+                    const int32_t u = child[(size_t)s * 4 + c];
+                    if (u < 0) continue;
+                    const uint32_t b = bfs_id[u];
+                    t->gotos[(size_t)i * 4 + c] = b | (t->own_off[b + 1] > t->own_off[b] ? AC_FLAG : 0u);
+                }
+            }
+        }
 
         // ---- two bases per lookup: delta2[s][x | y << 2] = delta(delta(s, x), y),
         // bit 31 = the final state has output, bit 30 = the state after x has output

@@ -27,11 +27,18 @@ struct HostTables {
     std::vector<uint32_t> pat_state;  // [P]
     std::vector<uint32_t> depth;      // [S]
     std::vector<uint32_t> fail;       // [S]
+    // failure-less form (built on request): trie edges and the keywords ending at each state
+    std::vector<uint32_t> gotos;      // [S*4] child | AC_FLAG (child has own keywords), or AC_NO_EDGE
+    std::vector<uint32_t> own_off;    // [S+1]
+    std::vector<uint32_t> own_pid;    // [P]
+    std::vector<uint32_t> own_len;    // [P] pat_len[own_pid[j]]
 };
+static constexpr uint32_t AC_NO_EDGE = 0x7fffffffu;
 
 // Builds the flattened machine on the host. Returns an ac_status.
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, uint32_t stride2_states, HostTables* t, uint32_t* bad_pattern);
+                  bool with_stride2, uint32_t stride2_states, bool with_failureless, HostTables* t,
+                  uint32_t* bad_pattern);
 
 struct ac_dfa {
     HostTables host;
@@ -43,6 +50,10 @@ struct ac_dfa {
     uint32_t* d_out_off = nullptr;
     uint32_t* d_out_pid = nullptr;
     uint32_t* d_out_len = nullptr;  // [E] keyword length of each output entry
+    uint32_t* d_gotos = nullptr;    // failure-less form (null unless built)
+    uint32_t* d_own_off = nullptr;
+    uint32_t* d_own_pid = nullptr;
+    uint32_t* d_own_len = nullptr;
     uint64_t device_bytes = 0;
     double build_ms = 0.0;
 };
@@ -161,6 +172,24 @@ struct PartArgs {
 // Launches grid (grid_x, n_parts) x threads, interleave 1.
 int ac_launch_part_scan(const PartArgs& a, uint32_t n_parts, uint32_t grid_x, uint32_t threads, uint32_t chunk,
                         void* stream);
+// Failure-less matching (ac_kernels.cu): one lane per start position.
+static constexpr uint32_t AC_STATE_MASK31 = 0x7fffffffu;
+struct FlArgs {
+    const uint32_t* gotos;    // [S*4] trie edges (AC_NO_EDGE where none), bit 31 = child has own keywords
+    const uint32_t* own_off;  // [S+1]
+    const uint32_t* own_pid;  // [P]
+    const uint32_t* own_len;  // [P] keyword length of each own_pid entry
+    const uint32_t* text;
+    uint64_t n;
+    uint64_t own_begin, own_end;
+    uint32_t halo;            // L_max - 1
+    uint32_t text_id;
+    ac_match* matches;
+    uint64_t capacity;
+    unsigned long long* counter;
+    unsigned long long* hits;  // [S] own-keyword hits per state
+};
+int ac_launch_failureless(const FlArgs& a, uint32_t hot, void* stream);
 // Sets the batch kernel's shared-memory limit for a shape (call before graph capture).
 int ac_prepare_batch(const ScanShape& sh);
 

@@ -443,6 +443,50 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
     }
 }
 
+// Failure-less matching (the PFAC scheme the paper cites in Sec. II): one
+// lane per start position walks only the trie edges from the root and stops
+// at the first missing edge; at every state it passes where keywords end
+// (own keywords, not inherited ones) it reports them with its start. Each
+// occurrence is found by the lane of its own start, so no failure
+// transitions are needed. Lanes run in lockstep over depth so the event
+// queue and drain of the main scan serve here too (pointed at the
+// own-keyword tables); ownership is by end position, as in the main scan.
+__global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t hot) {
+    extern __shared__ uint4 sm_rows[];
+    stage_hot(sm_rows, a.gotos, hot);
+    const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
+    const uint64_t pol_tab = policy_evict_last();
+    const Tables tb{nullptr, nullptr, 0u, a.own_off, a.own_pid, a.own_len};
+    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+    uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
+    const uint32_t lt = lanemask_lt();
+    const uint64_t first = a.own_begin > a.halo ? a.own_begin - a.halo : 0;  // starts whose ends can be owned
+    const uint64_t span = a.own_end - first;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t rounds = (span + T - 1) / T;  // uniform over the grid
+    uint32_t qn = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = first + r * T + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        bool alive = i < a.own_end;
+        uint32_t s = 0;
+        for (uint32_t k = 0; k <= a.halo && __any_sync(FULL, alive); ++k) {
+            const uint64_t p = i + k;
+            uint32_t e = AC_NO_EDGE;
+            if (alive && p < a.n) {
+                const uint32_t c = (__ldg(a.text + (p >> 4)) >> (2 * (p & 15))) & 3u;
+                const uint32_t idx = (s << 2) | c;
+                e = (s < hot) ? sm[idx] : ld_table(a.gotos + idx, pol_tab);
+            }
+            alive = alive && (e & AC_STATE_MASK31) != AC_NO_EDGE;
+            if (alive) s = e & AC_STATE_MASK31;
+            const bool h = alive && (e & AC_FLAG) && p >= a.own_begin && p < a.own_end;
+            const uint32_t m = __ballot_sync(FULL, h);
+            if (m) append(q, qn, m, h, p, s, a.text_id, lt, tb, sk);
+        }
+    }
+    if (qn) drain(q, qn, tb, sk);
+}
+
 __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint32_t* __restrict__ packed, int fold,
                             unsigned long long* bad) {
     const uint64_t nw = (n + 15) >> 4;
@@ -713,6 +757,21 @@ int ac_launch_part_scan(const PartArgs& a, uint32_t n_parts, uint32_t grid_x, ui
     int rc = set_smem(part_scan_kernel<1>, smem);
     if (rc) return rc;
     part_scan_kernel<1><<<dim3(grid_x, n_parts), threads, smem, (cudaStream_t)stream>>>(a, chunk, n_chunks);
+    return (int)cudaGetLastError();
+}
+
+int ac_launch_failureless(const FlArgs& a, uint32_t hot, void* stream) {
+    if (a.own_end <= a.own_begin) return 0;
+    const size_t smem = ac_scan_smem_bytes(hot, 1024, 1);
+    int rc = set_smem(failureless_kernel, smem);
+    if (rc) return rc;
+    const DeviceProps& p = ac_device_props();
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, failureless_kernel, 1024, smem);
+    const uint64_t span = a.own_end - (a.own_begin > a.halo ? a.own_begin - a.halo : 0);
+    const uint64_t want = (span + 1023) / 1024;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)p.sms * std::max(nb, 1));
+    failureless_kernel<<<grid, 1024, smem, (cudaStream_t)stream>>>(a, hot);
     return (int)cudaGetLastError();
 }
 

@@ -233,6 +233,33 @@ def test_two_base_table_can_be_skipped():
     assert d.info["table2_bytes"] == 0 and len(d.tables()["delta2"]) == 0
 
 
+def walk_failureless(t, text: bytes):
+    """From every start, follow trie edges only and report own keywords."""
+    g, off, pid = t["gotos"], t["own_off"], t["own_pid"]
+    out = set()
+    for i in range(len(text)):
+        s = 0
+        for j in range(i, len(text)):
+            e = int(g[4 * s + CODE[text[j]]])
+            if (e & 0x7FFFFFFF) == 0x7FFFFFFF:
+                break
+            s = e & 0x7FFFFFFF
+            assert bool(e >> 31) == (off[s + 1] > off[s])
+            out |= {(i, int(p)) for p in pid[off[s] : off[s + 1]]}
+    return out
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_failureless_tables_walk_equals_oracle(seed):
+    rng = random.Random(800 + seed)
+    pats = rand_set(rng, rng.randint(1, 40), 1, 8) + [b"AAA", b"A"]
+    text = bytes(rng.choice(b"ACGT") for _ in range(rng.choice([0, 1, 300, 1500]))) + b"AAAA"
+    t = acg.build(pats, host_only=True, failureless=True).tables()
+    pos, pid, _ = oracle.Machine(pats).scan(text)
+    assert walk_failureless(t, text) == set(zip(pos.tolist(), pid.tolist()))
+    assert "gotos" not in acg.build(pats, host_only=True).tables()
+
+
 def test_breadth_first_numbering():
     rng = random.Random(3)
     t = acg.build(rand_set(rng, 200, 5, 12), host_only=True).tables()
