@@ -586,6 +586,54 @@ def run_partition(args, steps: int = 3) -> dict:
     return {"workload": f"partition-{n}b-markov", "rows": out}
 
 
+# -------------------------------------------- failure-less comparison
+
+
+def run_failureless(args, steps: int = 3) -> dict:
+    """Failure-less matching (one thread per start position over the trie
+    edges, the scheme cited in Sec. II) against the failure-folded walk, on the
+    1 Mbase / 100-keyword, 256 Mbase / 10,000-keyword and a 1 Gbase slice of
+    the genome / 100,000-keyword workloads."""
+    import ctypes
+
+    import paper_1403_7294_gb300 as acg
+    from paper_1403_7294_gb300 import _native as N
+
+    lib = acg.lib()
+    sp = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for name, nb in (("small", None), ("chromosome", None), ("genome", 1_000_000_000)):
+        w = make_workload(name, nb, "cuda", 0)
+        n = int(w.text.ascii.numel())
+        packed = acg.pack(w.text.ascii)
+        del w.text.ascii
+        d = acg.build(w.patterns, failureless=True)
+        acg.autotune(d, packed, n)
+        desc = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
+        row = {"workload": w.name, "states": d.info["n_states"]}
+        for kind, fn in (("ac_walk", lib.ac_scan), ("failureless", lib.ac_scan_failureless)):
+            o = N.ScanOpts()
+            o.hot_states = -1
+            r0 = N.Result(None, 0, 0, None, 1, 0, 0)
+            fn(d.h, ctypes.byref(desc), ctypes.byref(r0), ctypes.byref(o), sp, None)
+            cap = int(r0.n_matches) + 16
+            raw = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
+            r = N.Result(raw.data_ptr(), cap, 0, None, 1, 0, 0)
+            st = N.ScanStats()
+            ms = []
+            for _ in range(steps + 1):
+                assert fn(d.h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(o), sp, ctypes.byref(st)) == 0
+                ms.append(st.scan_ms)
+            t = float(np.median(ms[1:]))
+            row[kind] = {"kernel_ms": round(t, 4), "gbases_s": round(n / t / 1e6, 2), "occurrences": int(r.n_matches)}
+        assert row["ac_walk"]["occurrences"] == row["failureless"]["occurrences"]
+        rows.append(row)
+        d.close()
+        del packed
+        torch.cuda.empty_cache()
+    return {"rows": rows}
+
+
 # ------------------------------------------------------- reference arm
 
 
@@ -645,7 +693,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["genome", "chromosome", "small", "batch", "serve", "partition"],
+    ap.add_argument("--workload",
+                    choices=["genome", "chromosome", "small", "batch", "serve", "partition", "failureless"],
                     default="genome")
     ap.add_argument("--n-bases", type=int, default=None)
     ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
@@ -674,6 +723,15 @@ def main():
                     "ms_per_step": b["graph_replay_ms"], "higher_is_better": True, "scaling": "weak",
                     "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": {"workload": b["workload"]},
                     "batched": b})
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "failureless":
+        fl = run_failureless(args)
+        out = {"metric": METRIC, "value": fl["rows"][-1]["ac_walk"]["gbases_s"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+               "config": {"workload": "failureless-comparison"}, "failureless": fl}
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
