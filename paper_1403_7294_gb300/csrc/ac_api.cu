@@ -502,6 +502,10 @@ int stage_packed(const ac_text* text, uint32_t fold, cudaStream_t st, Scratch& s
     return AC_OK;
 }
 
+constexpr uint64_t kPipePiece = 256ull << 20;  // owned bases per piece of a host-buffer scan
+int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts, cudaStream_t st,
+                   uint64_t own_begin, uint64_t own_end);
+
 }  // namespace
 
 // -------------------------------------------------------------------- scan
@@ -526,6 +530,8 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
     keep_pool_memory();
     cudaStream_t st = (cudaStream_t)stream;
+    if (!text->on_device && !r->on_device && !stats && own_end - own_begin >= 2 * kPipePiece)
+        return scan_pipelined(dfa, text, r, opts, st, own_begin, own_end);  // overlap copies with the scan
     Events ev(stats != nullptr, st);
     Scratch sc(st);
     cudaError_t e;
@@ -563,6 +569,213 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     return scan_core(dfa, words, n, own_begin, own_end, 0, r, opts, st, sc, d_ctr, d_hits,
                      text->encoding == AC_TEXT_ASCII, ev, stats);
 }
+
+// ------------------------------------------- host buffers: overlapped pieces
+// When the text and the results are both in host memory and the owned range
+// is long, the range is cut into pieces (64-base boundaries). Piece i's bases
+// are copied in on one stream, scanned on the caller's stream, and its
+// occurrences - which the occurrence counter places right after piece i-1's -
+// are copied out on a third stream while piece i+1 is being scanned. Same
+// results as the one-shot path.
+
+namespace {
+
+constexpr int kPipeMaxPieces = 64;
+
+struct CopyStreams {
+    cudaStream_t in = nullptr, out = nullptr;
+};
+
+const CopyStreams& copy_streams() {
+    static CopyStreams cs[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    std::call_once(once[dev], [dev] {
+        cudaStreamCreateWithFlags(&cs[dev].in, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&cs[dev].out, cudaStreamNonBlocking);
+    });
+    return cs[dev];
+}
+
+unsigned long long* pinned_counts() {  // one pinned slot per piece, per host thread
+    static thread_local unsigned long long* pad = nullptr;
+    if (!pad && cudaMallocHost(&pad, (kPipeMaxPieces + 2) * sizeof(unsigned long long)) != cudaSuccess) pad = nullptr;
+    return pad;
+}
+
+int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts, cudaStream_t st,
+                   uint64_t own_begin, uint64_t own_end) {
+    const HostTables& h = dfa->host;
+    const uint64_t n = text->n_bases;
+    const bool ascii = text->encoding == AC_TEXT_ASCII;
+    const uint32_t fold = opts ? (opts->flags & AC_SCAN_FOLD_CASE) : 0u;
+    const uint64_t halo = h.max_len - 1;
+    const uint64_t owned = own_end - own_begin;
+    const uint64_t piece = std::max<uint64_t>(kPipePiece, round_up((owned + kPipeMaxPieces - 1) / kPipeMaxPieces, 64));
+    const CopyStreams& cs = copy_streams();
+    unsigned long long* pad = pinned_counts();
+    if (!pad || !cs.in || !cs.out) return AC_ERR_CUDA;
+    Scratch sc(st);
+    cudaError_t e;
+    void* d_src = nullptr;  // the text as given (ASCII bytes or packed words)
+    uint32_t* d_words = nullptr;
+    unsigned long long *d_ctr = nullptr, *d_hits = nullptr, *d_counts = nullptr;
+    ac_match* d_m = nullptr;
+    if ((e = sc.get(&d_src, round_up(text_bytes(*text), 16))) != cudaSuccess) return cuda_status(e);
+    if (ascii && (e = sc.get((void**)&d_words, round_up((n + 15) / 16 * 4, 16))) != cudaSuccess)
+        return cuda_status(e);
+    if (!ascii) d_words = (uint32_t*)d_src;
+    if ((e = sc.get((void**)&d_ctr, 4 * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = sc.get((void**)&d_m, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
+    if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr, 0, 16, st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 16, st)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
+    cudaEvent_t ready, in_done[kPipeMaxPieces], cnt_done[kPipeMaxPieces], out_done;
+    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&out_done, cudaEventDisableTiming);
+    for (int i = 0; i < kPipeMaxPieces; ++i) {
+        cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&cnt_done[i], cudaEventDisableTiming);
+    }
+    cudaEventRecord(ready, st);  // scratch allocated and cleared
+    cudaStreamWaitEvent(cs.in, ready, 0);
+    const ScanShape full = ac_default_shape(dfa, owned, opts);
+    const DeviceProps& p = ac_device_props();
+    const uint64_t lanes = (uint64_t)p.sms * full.blocks_per_sm * full.threads * full.interleave;
+    int status = AC_OK;
+    uint64_t copied = (own_begin > halo ? own_begin - halo : 0) & ~63ull;  // bases on the device so far
+    uint64_t out_from = 0;                                                 // occurrences already copied out
+    int k = 0;
+    for (uint64_t a = own_begin, b = 0; a < own_end && status == AC_OK; a = b, ++k) {
+        // piece boundaries on absolute 64-base multiples (word-aligned packing); the last takes the rest
+        b = (k == kPipeMaxPieces - 1) ? own_end : std::min<uint64_t>(own_end, (a + piece) & ~63ull);
+        const uint64_t upto = (b == own_end) ? n : b;  // bases the piece needs
+        // ---- copy in [copied, upto)
+        if (upto > copied) {
+            if (ascii) {
+                e = cudaMemcpyAsync((uint8_t*)d_src + copied, (const uint8_t*)text->data + copied, upto - copied,
+                                    cudaMemcpyHostToDevice, cs.in);
+            } else {
+                const uint64_t w0 = copied / 16, w1 = (upto + 15) / 16;
+                e = cudaMemcpyAsync((uint32_t*)d_src + w0, (const uint32_t*)text->data + w0, (w1 - w0) * 4,
+                                    cudaMemcpyHostToDevice, cs.in);
+            }
+            if (e != cudaSuccess) {
+                status = cuda_status(e);
+                break;
+            }
+        }
+        cudaEventRecord(in_done[k], cs.in);
+        cudaStreamWaitEvent(st, in_done[k], 0);
+        if (ascii && upto > copied) {  // copied is a multiple of 64 bases, so packing stays word-aligned
+            // d_ctr[3] records that some piece had a bad byte (offset relative to the piece)
+            const int rc = ac_launch_pack((const uint8_t*)d_src + copied, upto - copied, d_words + copied / 16,
+                                          fold != 0, d_ctr + 3, st);
+            if (rc) {
+                status = cuda_status((cudaError_t)rc);
+                break;
+            }
+        }
+        copied = std::max(copied, upto);
+        // ---- scan the owned piece
+        ScanShape sh = full;  // shape of the whole range; chunks re-sized to the piece unless given
+        const uint64_t len = b - a;
+        if (!(opts && opts->chunk))
+            sh.chunk = (uint32_t)std::min<uint64_t>(std::max<uint64_t>((len + lanes - 1) / std::max<uint64_t>(lanes, 1),
+                                                                       std::max<uint64_t>(64, round_up(halo, 64))),
+                                                    1u << 30);
+        const uint64_t nch = (len + sh.chunk - 1) / sh.chunk;
+        sh.grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (nch + (uint64_t)sh.threads * sh.interleave - 1) /
+                                                                      ((uint64_t)sh.threads * sh.interleave)),
+                                               (uint64_t)p.sms * sh.blocks_per_sm);
+        ScanArgs sa;
+        sa.delta = dfa->d_delta;
+        sa.delta2 = dfa->d_delta2;
+        sa.s2_rows = h.s2_rows;
+        sa.out_off = dfa->d_out_off;
+        sa.out_pid = dfa->d_out_pid;
+        sa.out_len = dfa->d_out_len;
+        sa.n_states = h.n_states;
+        sa.text = d_words;
+        sa.n = n;
+        sa.own_begin = a;
+        sa.own_end = b;
+        sa.halo = (uint32_t)halo;
+        sa.text_id = opts ? opts->text_id : 0u;
+        sa.matches = d_m;
+        sa.capacity = r->capacity;
+        sa.counter = d_ctr;
+        sa.hits = d_hits;
+        sa.pos_offset = 0;
+        int rc = ac_launch_scan(sa, sh, st);
+        if (rc) {
+            status = cuda_status((cudaError_t)rc);
+            break;
+        }
+        cudaMemcpyAsync(pad + k, d_ctr, 8, cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(cnt_done[k], st);
+        // ---- while piece k runs: copy out piece k-1's occurrences
+        if (k > 0) {
+            cudaEventSynchronize(cnt_done[k - 1]);
+            const uint64_t to = std::min<uint64_t>(pad[k - 1], r->capacity);
+            if (to > out_from) {
+                cudaStreamWaitEvent(cs.out, cnt_done[k - 1], 0);
+                cudaMemcpyAsync(r->matches + out_from, d_m + out_from, (to - out_from) * sizeof(ac_match),
+                                cudaMemcpyDeviceToHost, cs.out);
+                out_from = to;
+            }
+        }
+    }
+    if (status == AC_OK && d_counts) {
+        if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) status = cuda_status(e);
+        const int rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, st);
+        if (status == AC_OK && rc) status = cuda_status((cudaError_t)rc);
+    }
+    if (status == AC_OK) {
+        cudaMemcpyAsync(pad + kPipeMaxPieces, d_ctr, 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pad + kPipeMaxPieces + 1, d_ctr + 3, 8, cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) status = cuda_status(e);
+    }
+    if (status == AC_OK && ascii && pad[kPipeMaxPieces + 1] != ~0ull) {
+        // a bad byte somewhere: pack the whole text once more for its absolute offset
+        const int rc = ac_launch_pack((const uint8_t*)d_src, n, d_words, fold != 0, d_ctr + 2, st);
+        cudaMemcpyAsync(pad + kPipeMaxPieces + 1, d_ctr + 2, 8, cudaMemcpyDeviceToHost, st);
+        if (rc || (e = cudaStreamSynchronize(st)) != cudaSuccess) status = AC_ERR_CUDA;
+    }
+    if (status == AC_OK) {
+        const uint64_t nm = pad[kPipeMaxPieces];
+        const uint64_t bad = ascii ? pad[kPipeMaxPieces + 1] : ~0ull;
+        r->n_matches = nm;
+        r->bad_offset = bad;
+        const uint64_t to = std::min<uint64_t>(nm, r->capacity);
+        if (to > out_from)
+            cudaMemcpyAsync(r->matches + out_from, d_m + out_from, (to - out_from) * sizeof(ac_match),
+                            cudaMemcpyDeviceToHost, cs.out);
+        if (r->counts) cudaMemcpyAsync(r->counts, d_counts, (size_t)h.n_patterns * 8, cudaMemcpyDeviceToHost, cs.out);
+        if ((e = cudaStreamSynchronize(cs.out)) != cudaSuccess) status = cuda_status(e);
+        if (status == AC_OK) status = bad != ~0ull ? AC_ERR_ALPHABET : (nm > r->capacity ? AC_ERR_OVERFLOW : AC_OK);
+    }
+    // the scratch is released on `st`; make it wait for the copy streams first
+    cudaEventRecord(out_done, cs.out);
+    cudaStreamWaitEvent(st, out_done, 0);
+    cudaEventRecord(ready, cs.in);
+    cudaStreamWaitEvent(st, ready, 0);
+    cudaStreamSynchronize(cs.in);
+    cudaStreamSynchronize(cs.out);
+    cudaEventDestroy(ready);
+    cudaEventDestroy(out_done);
+    for (int i = 0; i < kPipeMaxPieces; ++i) {
+        cudaEventDestroy(in_done[i]);
+        cudaEventDestroy(cnt_done[i]);
+    }
+    return status;
+}
+
+}  // namespace
 
 // ------------------------------------------------------ failure-less scan
 
