@@ -352,12 +352,19 @@ def lookup_probe(packed: torch.Tensor, n: int, steps: int = 3) -> dict:
 # --------------------------------------------------------- CPU baseline
 
 
-def oracle_throughput(patterns, ascii_host: np.ndarray, target_s: float = 12.0):
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_throughput(patterns, ascii_host: np.ndarray, target_s: float = 12.0, machine=None):
     """Single-threaded oracle over a bounded prefix of the workload text."""
     import oracle
 
     t0 = time.perf_counter()
-    m = oracle.Machine(patterns)
+    m = machine if machine is not None else oracle.Machine(patterns)
     build_s = time.perf_counter() - t0
     probe = min(len(ascii_host), 2_000_000)
     t0 = time.perf_counter()
@@ -367,15 +374,104 @@ def oracle_throughput(patterns, ascii_host: np.ndarray, target_s: float = 12.0):
     t0 = time.perf_counter()
     pos, _, _ = m.scan(ascii_host[:k])
     dt = time.perf_counter() - t0
-    m.close()
     return k, dt, build_s, len(pos)
 
 
+def oracle_threaded(patterns, ascii_host: np.ndarray, threads: int, rate1: float, machine, target_s: float = 6.0):
+    """The oracle's two threaded forms (Sec. IV.A approaches 1 and 2) at
+    ``threads`` host threads, each on a prefix sized for about target_s."""
+    import oracle
+
+    lmax = max(len(p) for p in patterns)
+    rows = []
+    k = int(min(len(ascii_host), max(1 << 20, rate1 * threads * target_s)))
+    t0 = time.perf_counter()
+    pos, _, _ = oracle.scan_text_chunks(machine, ascii_host[:k], threads, lmax)
+    dt = time.perf_counter() - t0
+    rows.append({"form": "text ranges with an L_max-1 halo (approach 1)", "threads": threads,
+                 "value": round(k / dt / 1e9, 6), "unit": UNIT, "bases": k, "occurrences": int(len(pos)),
+                 "seconds": round(dt, 2)})
+    split = oracle.pattern_split(patterns, threads)
+    t0 = time.perf_counter()
+    machines = oracle._run_threads([lambda piece=piece: oracle.Machine(piece) for _, piece in split], threads)
+    build_s = time.perf_counter() - t0
+    k = int(min(len(ascii_host), max(1 << 20, rate1 * target_s)))
+    t0 = time.perf_counter()
+    pos, _, _ = oracle.scan_pattern_split(split, ascii_host[:k], threads, machines)
+    dt = time.perf_counter() - t0
+    for mm in machines:
+        mm.close()
+    rows.append({"form": "keyword list split, one machine per thread (approach 2, the paper's)",
+                 "threads": threads, "value": round(k / dt / 1e9, 6), "unit": UNIT, "bases": k,
+                 "occurrences": int(len(pos)), "seconds": round(dt, 2), "build_s": round(build_s, 2)})
+    return rows
+
+
 def cpu_baseline(patterns, ascii_host):
+    import oracle
+
+    m = oracle.Machine(patterns)
     k, dt, build_s, occ = oracle_throughput(patterns, ascii_host)
-    return {"value": round(k / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {k} bases of the workload text ({occ} occurrences), machine of all "
-                      f"{len(patterns)} keywords built once in {build_s:.1f}s (not timed); {dt:.1f}s of scan"}
+    out = {"value": round(k / dt / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {k} bases of the workload text ({occ} occurrences), machine of all "
+                     f"{len(patterns)} keywords built once in {build_s:.1f}s (not timed); {dt:.1f}s of scan"}
+    out["threaded"] = oracle_threaded(patterns, ascii_host, host_threads(), k / dt, m)
+    m.close()
+    return out
+
+
+def run_cpu_sweep(args, rank):
+    """Host analogue of the paper's thread-count figures (Sec. V, Fig. 4-5):
+    the oracle's two threaded forms at 1, 2, 4, ... host threads on a prefix
+    of the workload text, with the speed-up over one thread."""
+    if rank != 0:
+        return None
+    import oracle
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    # without a GPU to draw the full genome, a sample-sized text of the same model (its own keywords)
+    w = make_workload("genome", args.n_bases if dev == "cuda" else args.sweep_bases, dev, 0)
+    n_sample = min(int(w.text.ascii.numel()), args.sweep_bases)
+    text = w.text.ascii[:n_sample].cpu().numpy()
+    del w.text.ascii
+    T = host_threads()
+    counts = sorted({1, T} | {1 << i for i in range(8) if (1 << i) < T})
+    m = oracle.Machine(w.patterns)
+    lmax = max(len(p) for p in w.patterns)
+    rows = []
+    for form in ("text", "patterns"):
+        base = None
+        split_cache = {}
+        for t in counts:
+            if form == "text":
+                t0 = time.perf_counter()
+                pos, _, _ = oracle.scan_text_chunks(m, text, t, lmax)
+                dt = time.perf_counter() - t0
+                extra = {}
+            else:
+                split = split_cache.setdefault(t, oracle.pattern_split(w.patterns, t))
+                t0 = time.perf_counter()
+                machines = oracle._run_threads([lambda piece=piece: oracle.Machine(piece) for _, piece in split], t)
+                build_s = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                pos, _, _ = oracle.scan_pattern_split(split, text, t, machines)
+                dt = time.perf_counter() - t0
+                for mm in machines:
+                    mm.close()
+                extra = {"build_s": round(build_s, 3)}
+            base = base or dt
+            rows.append({"form": form, "threads": t, "seconds": round(dt, 3), "gbases_s": round(n_sample / dt / 1e9, 6),
+                         "speedup": round(base / dt, 2), "occurrences": int(len(pos)), **extra})
+            log(f"[bench/sweep] {form} T={t}: {dt:.2f}s")
+    best = max(rows, key=lambda r: r["gbases_s"])
+    return {"impl": "reference", "metric": METRIC, "value": best["gbases_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": round(n_sample / best["gbases_s"] / 1e6, 3),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"cpu-sweep-{w.name}-first{n_sample}b", "host_threads": T},
+            "cpu_baseline": {"value": best["gbases_s"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
+                             "sample": f"first {n_sample} bases of {w.name}"},
+            "e2e": {"value": best["gbases_s"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sweep": rows}
 
 
 # --------------------------------------------------------- batched (cfg 4)
@@ -694,8 +790,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload",
-                    choices=["genome", "chromosome", "small", "batch", "serve", "partition", "failureless"],
+                    choices=["genome", "chromosome", "small", "batch", "serve", "partition", "failureless",
+                             "cpu-sweep"],
                     default="genome")
+    ap.add_argument("--sweep-bases", type=int, default=32_000_000,
+                    help="cpu-sweep: bases of the genome text each thread count scans")
     ap.add_argument("--n-bases", type=int, default=None)
     ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
     ap.add_argument("--serve-seconds", type=float, default=None)
@@ -706,6 +805,11 @@ def main():
         log("[bench] warmup raised to 3")
         args.warmup = 3
     world, rank, local = dist_setup()
+    if args.workload == "cpu-sweep":  # the oracle only (host threads), either --impl
+        out = run_cpu_sweep(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, world, rank)
         if out is not None:

@@ -203,3 +203,89 @@ def canonical(pos: np.ndarray, pid: np.ndarray, text_id: np.ndarray | None = Non
     out["pid"] = pid
     out.sort(order=["text_id", "pos", "pid"])
     return out
+
+
+# ------------------------------------------------ the two threaded forms (Sec. IV.A)
+
+
+def _text_array(text) -> np.ndarray:
+    if isinstance(text, np.ndarray):
+        return np.ascontiguousarray(text, dtype=np.uint8)
+    return np.frombuffer(_as_bytes(text), dtype=np.uint8)
+
+
+def _run_threads(jobs, threads: int):
+    from concurrent.futures import ThreadPoolExecutor
+
+    if threads <= 1:
+        return [j() for j in jobs]
+    with ThreadPoolExecutor(max_workers=threads) as ex:  # each job is one C call (GIL released)
+        return list(ex.map(lambda j: j(), jobs))
+
+
+def scan_text_chunks(machine: Machine, text, threads: int, max_len: int):
+    """Approach 1 of Sec. IV.A, made exact: the text's end positions are split
+    into ``threads`` contiguous ranges; thread t scans its range preceded by
+    the ``max_len - 1`` bases before it, from the root, and keeps only the
+    occurrences that end inside its range (each occurrence has one end).
+    All threads share the one machine (read only). Returns (pos, pid, counts)
+    in range order."""
+    t = _text_array(text)
+    n = t.size
+    k = max(1, int(threads))
+    bounds = [n * i // k for i in range(k + 1)]
+
+    def job(i):
+        a, b = bounds[i], bounds[i + 1]
+        lo = max(0, a - (max_len - 1))
+        pos, pid, _ = machine.scan(t[lo:b])
+        return pos + np.uint64(lo), pid
+
+    parts = _run_threads([lambda i=i: job(i) for i in range(k)], k)
+    pos = np.concatenate([p for p, _ in parts]) if parts else np.empty(0, np.uint64)
+    pid = np.concatenate([q for _, q in parts]) if parts else np.empty(0, np.uint32)
+    if pos.size:
+        lens = machine._args.lens.astype(np.uint64)
+        end = pos + lens[pid] - np.uint64(1)
+        # range i keeps ends in [bounds[i], bounds[i+1]); ranges were scanned in order
+        owner = np.searchsorted(np.asarray(bounds[1:], dtype=np.uint64), end, side="right")
+        which = np.repeat(np.arange(k), [p.size for p, _ in parts])
+        keep = owner == which
+        pos, pid = pos[keep], pid[keep]
+    counts = np.bincount(pid, minlength=machine.n_patterns).astype(np.uint64)
+    return pos, pid, counts
+
+
+def pattern_split(patterns: Sequence, parts: int) -> list[tuple[int, list]]:
+    """Approach 2 of Sec. IV.A (Fig. 3): the keyword list cut into ``parts``
+    consecutive pieces of near-equal size; each piece keeps the id of its
+    first keyword so that local ids map back by an offset."""
+    p = list(patterns)
+    k = max(1, min(int(parts), len(p)))
+    cut = [len(p) * i // k for i in range(k + 1)]
+    return [(cut[i], p[cut[i] : cut[i + 1]]) for i in range(k)]
+
+
+def scan_pattern_split(split, text, threads: int, machines: list | None = None):
+    """Approach 2 of Sec. IV.A (Fig. 3): one machine per piece of the keyword
+    list, every thread scanning the whole text with its own machine; the
+    union of the pieces' occurrences with ids offset is the whole set's.
+    ``machines`` (one per piece) skips the builds; otherwise each thread
+    builds its own machine first, as in the paper. Returns (pos, pid,
+    counts)."""
+    t = _text_array(text)
+
+    def job(i):
+        off, pats = split[i]
+        m = machines[i] if machines is not None else Machine(pats)
+        pos, pid, c = m.scan(t)
+        return pos, pid + np.uint32(off), off, c
+
+    res = _run_threads([lambda i=i: job(i) for i in range(len(split))], threads)
+    total = sum(len(p) for _, p in split)
+    counts = np.zeros(total, dtype=np.uint64)
+    for _, _, off, c in res:
+        counts[off : off + c.size] = c
+    pos = np.concatenate([r[0] for r in res]) if res else np.empty(0, np.uint64)
+    pid = np.concatenate([r[1] for r in res]) if res else np.empty(0, np.uint32)
+    return pos, pid, counts

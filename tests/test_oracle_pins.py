@@ -287,6 +287,40 @@ def test_text_chunks_with_halo_equal_one_pass():
         assert sorted(got) == full, C
 
 
+def test_threaded_forms_equal_bruteforce():
+    """The oracle's two threaded forms of Sec. IV.A (approach 1: text ranges
+    with an L_max-1 halo, ownership by end; approach 2: the keyword list split
+    into pieces, one machine each) against brute force, with more threads
+    than bases, than keywords, and ranges shorter than L_max."""
+    rng = random.Random(24)
+    for case in range(120):
+        pats, text = fuzz_case(rng)
+        want = brute(pats, text)
+        hist = np.zeros(len(pats), np.int64)
+        for _, q in want:
+            hist[q] += 1
+        m = oracle.Machine(pats)
+        lmax = max(len(p) for p in pats)
+        for T in (1, 2, 5, 33):
+            p1, q1, c1 = oracle.scan_text_chunks(m, text, T, lmax)
+            assert len(p1) == len(want) and as_set(p1, q1) == want, (case, T)
+            assert c1.tolist() == hist.tolist()
+            p2, q2, c2 = oracle.scan_pattern_split(oracle.pattern_split(pats, T), text, T)
+            assert len(p2) == len(want) and as_set(p2, q2) == want, (case, T)
+            assert c2.tolist() == hist.tolist()
+
+
+def test_pattern_split_pieces():
+    pats = [f"A{i}" for i in range(10)]
+    for k in (1, 3, 10, 25):
+        split = oracle.pattern_split(pats, k)
+        assert len(split) == min(k, 10)
+        assert [p for _, piece in split for p in piece] == pats
+        assert all(off == sum(len(x) for _, x in split[:i]) for i, (off, _) in enumerate(split))
+        sizes = [len(x) for _, x in split]
+        assert max(sizes) - min(sizes) <= 1
+
+
 def test_counts_sum_to_occurrences():
     rng = random.Random(23)
     text = "".join(rng.choice("AC") for _ in range(20000))  # repeat-rich
