@@ -292,15 +292,18 @@ def run_plain(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
+    call_ms = []
     for _ in range(k_e2e):
+        t1 = time.perf_counter()
         s = lib.ac_scan(dfa.h, ctypes.byref(desc_h), ctypes.byref(res_h), ctypes.byref(opts), sp, None)
         assert s == N.AC_OK, s
+        call_ms.append(round((time.perf_counter() - t1) * 1e3, 2))  # ac_scan returns with its results on the host
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     assert int(res_h.n_matches) == n_matches and int(cnt_h.sum()) == n_matches
     out["e2e"] = {"value": round(k_e2e * n * world / e2e_s / 1e9, 3), "unit": UNIT,
                   "h2d_bytes_per_step": int(host_packed.numel() * 4),
-                  "d2h_bytes_per_step": int(16 * n_matches + 8 * P + 16), "steps": k_e2e}
+                  "d2h_bytes_per_step": int(16 * n_matches + 8 * P + 16), "steps": k_e2e, "call_ms": call_ms}
     del host_packed, raw_h
     return out, (dfa, w, ascii_prefix)
 
@@ -730,6 +733,76 @@ def run_failureless(args, steps: int = 3) -> dict:
     return {"rows": rows}
 
 
+def run_stream(args, steps: int = 3) -> dict:
+    """A long text delivered in consecutive device-resident pieces through
+    ac_stream_scan (carried L_max-1 bases, global positions) against one
+    ac_scan of the whole text, at several piece sizes; both wall-clock timed
+    per pass (every call returns its exact occurrence count)."""
+    import ctypes
+
+    import paper_1403_7294_gb300 as acg
+    from paper_1403_7294_gb300 import _native as N
+
+    lib = acg.lib()
+    sp = torch.cuda.current_stream().cuda_stream
+    w = make_workload("genome", args.n_bases, "cuda", 0)
+    n = int(w.text.ascii.numel())
+    packed = acg.pack(w.text.ascii)
+    del w.text.ascii
+    torch.cuda.empty_cache()
+    d = acg.build(w.patterns)
+    acg.autotune(d, packed, n)
+    o = N.ScanOpts()
+    o.hot_states = -1
+    whole = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
+    r0 = N.Result(None, 0, 0, None, 1, 0, 0)
+    lib.ac_scan(d.h, ctypes.byref(whole), ctypes.byref(r0), ctypes.byref(o), sp, None)
+    k = int(r0.n_matches)
+    raw = torch.empty((k + 16, 2), dtype=torch.int64, device="cuda")
+    cnt = torch.empty(len(w.patterns), dtype=torch.int64, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            got = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            assert got == k, (got, k)
+        return float(np.median(ts))
+
+    def one_shot():
+        r = N.Result(raw.data_ptr(), k + 16, 0, cnt.data_ptr(), 1, 0, 0)
+        assert lib.ac_scan(d.h, ctypes.byref(whole), ctypes.byref(r), ctypes.byref(o), sp, None) == 0
+        return int(r.n_matches)
+
+    t_one = timed(one_shot)
+    rows = []
+    s = acg.Stream(d)
+    for piece in (1 << 24, 1 << 26, 1 << 28):
+        spans = [(a, min(piece, n - a)) for a in range(0, n, piece)]
+
+        def streamed():
+            assert lib.ac_stream_reset(s.h) == 0
+            got = 0
+            for a, ln in spans:  # a is a multiple of 16 bases: the piece starts on a word
+                desc = N.Text(packed.data_ptr() + a // 4, ln, N.AC_TEXT_PACKED2, 1)
+                r = N.Result(raw.data_ptr() + 16 * got, k + 16 - got, 0, cnt.data_ptr(), 1, 0, 0)
+                assert lib.ac_stream_scan(s.h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(o), sp, None) == 0
+                got += int(r.n_matches)
+            return got
+
+        t = timed(streamed)
+        rows.append({"piece_bases": piece, "pieces": len(spans), "wall_ms": round(t * 1e3, 3),
+                     "gbases_s": round(n / t / 1e9, 2)})
+        log(f"[bench/stream] piece {piece}: {t * 1e3:.2f} ms")
+    s.close()
+    return {"workload": f"stream-{w.name}", "occurrences": k,
+            "one_shot": {"wall_ms": round(t_one * 1e3, 3), "gbases_s": round(n / t_one / 1e9, 2)}, "rows": rows}
+
+
 # ------------------------------------------------------- reference arm
 
 
@@ -791,7 +864,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload",
                     choices=["genome", "chromosome", "small", "batch", "serve", "partition", "failureless",
-                             "cpu-sweep"],
+                             "stream", "cpu-sweep"],
                     default="genome")
     ap.add_argument("--sweep-bases", type=int, default=32_000_000,
                     help="cpu-sweep: bases of the genome text each thread count scans")
@@ -836,6 +909,15 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                "config": {"workload": "failureless-comparison"}, "failureless": fl}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "stream":
+        sm = run_stream(args)
+        best = max(r["gbases_s"] for r in sm["rows"])
+        out = {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": 3, "warmup": 1,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+               "data": "synthetic", "config": {"workload": sm["workload"]}, "stream": sm}
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

@@ -162,13 +162,13 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
         struct Up {
             uint32_t** dst;
             const std::vector<uint32_t>* src;
-        } ups[] = {{&d->d_delta, &h.delta}, {&d->d_out_off, &h.out_off}, {&d->d_out_pid, &h.out_pid},
-                   {&d->d_out_len, &h.out_len}, {&d->d_delta2, &h.delta2}, {&d->d_gotos, &h.gotos},
-                   {&d->d_own_off, &h.own_off}, {&d->d_own_pid, &h.own_pid}, {&d->d_own_len, &h.own_len}};
+        } ups[] = {{&d->d_delta, &h.delta},   {&d->d_out_off, &h.out_off}, {&d->d_out_ent, &h.out_ent},
+                   {&d->d_delta2, &h.delta2}, {&d->d_gotos, &h.gotos},     {&d->d_own_off, &h.own_off},
+                   {&d->d_own_ent, &h.own_ent}};
         cudaError_t e = cudaSuccess;
         for (auto& u : ups) {
-            const bool optional = u.dst == &d->d_delta2 || u.dst == &d->d_gotos || u.dst == &d->d_own_off ||
-                                  u.dst == &d->d_own_pid || u.dst == &d->d_own_len;
+            const bool optional =
+                u.dst == &d->d_delta2 || u.dst == &d->d_gotos || u.dst == &d->d_own_off || u.dst == &d->d_own_ent;
             if (optional && u.src->empty()) continue;  // two-base / failure-less tables not built
             const size_t bytes = std::max<size_t>(u.src->size(), 1) * sizeof(uint32_t);
             e = dev_alloc((void**)u.dst, bytes);
@@ -190,7 +190,7 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
 
 extern "C" void ac_free(ac_dfa* d) {
     if (!d) return;
-    if (d->d_delta || d->d_delta2 || d->d_out_off || d->d_out_pid || d->d_out_len) {
+    if (d->d_delta || d->d_delta2 || d->d_out_off || d->d_out_ent) {
         int cur = 0;
         cudaGetDevice(&cur);
         if (d->device >= 0) cudaSetDevice(d->device);
@@ -198,12 +198,10 @@ extern "C" void ac_free(ac_dfa* d) {
         cudaFree(d->d_delta);
         cudaFree(d->d_delta2);
         cudaFree(d->d_out_off);
-        cudaFree(d->d_out_pid);
-        cudaFree(d->d_out_len);
+        cudaFree(d->d_out_ent);
         cudaFree(d->d_gotos);
         cudaFree(d->d_own_off);
-        cudaFree(d->d_own_pid);
-        cudaFree(d->d_own_len);
+        cudaFree(d->d_own_ent);
         cudaSetDevice(cur);
     }
     delete d;
@@ -379,8 +377,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
         FlArgs f;
         f.gotos = dfa->d_gotos;
         f.own_off = dfa->d_own_off;
-        f.own_pid = dfa->d_own_pid;
-        f.own_len = dfa->d_own_len;
+        f.own_ent = reinterpret_cast<const uint2*>(dfa->d_own_ent);
         f.text = words;
         f.n = n;
         f.own_begin = own_begin;
@@ -397,7 +394,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
         ev.rec(4);
         if (d_counts) {
             if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
-            rc = ac_launch_counts(dfa->d_own_off, dfa->d_own_pid, h.n_states, d_hits, d_counts, st);
+            rc = ac_launch_counts(dfa->d_own_off, reinterpret_cast<const uint2*>(dfa->d_own_ent), h.n_states, d_hits, d_counts, st);
             if (rc) return cuda_status((cudaError_t)rc);
         }
         ev.rec(5);
@@ -428,8 +425,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
-    a.out_pid = dfa->d_out_pid;
-    a.out_len = dfa->d_out_len;
+    a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
     a.text = words;
     a.n = n;
@@ -448,7 +444,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
     ev.rec(4);
     if (d_counts) {
         if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
-        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, st);
+        rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, d_hits, d_counts, st);
         if (rc) return cuda_status((cudaError_t)rc);
     }
     ev.rec(5);
@@ -697,8 +693,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
         sa.delta2 = dfa->d_delta2;
         sa.s2_rows = h.s2_rows;
         sa.out_off = dfa->d_out_off;
-        sa.out_pid = dfa->d_out_pid;
-        sa.out_len = dfa->d_out_len;
+        sa.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
         sa.n_states = h.n_states;
         sa.text = d_words;
         sa.n = n;
@@ -732,7 +727,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
     }
     if (status == AC_OK && d_counts) {
         if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) status = cuda_status(e);
-        const int rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, st);
+        const int rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, d_hits, d_counts, st);
         if (status == AC_OK && rc) status = cuda_status((cudaError_t)rc);
     }
     if (status == AC_OK) {
@@ -1056,7 +1051,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
     uint64_t off = 0;
     for (uint32_t i = 0; i < k; ++i) {
         const ac_dfa* d = set->parts[i];
-        pd[i] = PartDesc{d->d_delta, d->d_out_off, d->d_out_pid, d->d_out_len, d_hits + off, d->host.n_states,
+        pd[i] = PartDesc{d->d_delta, d->d_out_off, reinterpret_cast<const uint2*>(d->d_out_ent), d_hits + off, d->host.n_states,
                          set->first_pid[i]};
         off += d->host.n_states;
     }
@@ -1103,7 +1098,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
         if ((e = cudaMemsetAsync(d_counts, 0, (size_t)set->n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
         for (uint32_t i = 0; i < k; ++i) {
             const ac_dfa* d = set->parts[i];
-            rc = ac_launch_counts(d->d_out_off, d->d_out_pid, d->host.n_states, pd[i].hits, d_counts + set->first_pid[i],
+            rc = ac_launch_counts(d->d_out_off, reinterpret_cast<const uint2*>(d->d_out_ent), d->host.n_states, pd[i].hits, d_counts + set->first_pid[i],
                                   st);
             if (rc) return cuda_status((cudaError_t)rc);
         }
@@ -1272,8 +1267,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
-    a.out_pid = dfa->d_out_pid;
-    a.out_len = dfa->d_out_len;
+    a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
     a.texts = d_bt;
     a.item_prefix = d_prefix;
@@ -1291,7 +1285,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     ev.rec(4);
     if (d_counts) {
         if ((e = cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, st)) != cudaSuccess) return cuda_status(e);
-        rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, d_hits, d_counts, stream);
+        rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, d_hits, d_counts, stream);
         if (rc) return cuda_status((cudaError_t)rc);
     }
     ev.rec(5);
@@ -1395,8 +1389,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
-    a.out_pid = dfa->d_out_pid;
-    a.out_len = dfa->d_out_len;
+    a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
     a.texts = p->d_bt;
     a.item_prefix = p->d_prefix;
@@ -1422,7 +1415,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
         rc = ac_launch_batch(a, sh, cap);
         if (d_counts) {
             cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, cap);
-            if (!rc) rc = ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, p->d_hits, d_counts, cap);
+            if (!rc) rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, p->d_hits, d_counts, cap);
         }
         cudaMemcpyAsync(p->h_pad, p->d_ctr, 8, cudaMemcpyDeviceToHost, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);

@@ -175,14 +175,18 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
         t->pat_len.assign(lens, lens + n);
         t->pat_state.resize(n);
         for (uint32_t p = 0; p < n; ++p) t->pat_state[p] = bfs_id[pat_node[p]];
-        t->out_len.resize(E);
-        for (uint64_t k = 0; k < E; ++k) t->out_len[k] = lens[t->out_pid[k]];
+        t->out_ent.resize(2 * E);
+        for (uint64_t k = 0; k < E; ++k) {
+            t->out_ent[2 * k] = t->out_pid[k];
+            t->out_ent[2 * k + 1] = lens[t->out_pid[k]];
+        }
 
         // ---- failure-less form (trie edges only): goto[s][c] = child or AC_NO_EDGE,
         // bit 31 = the child is where some keyword ends; own keywords per state as CSR
         t->gotos.clear();
         t->own_off.clear();
         t->own_pid.clear();
+        t->own_ent.clear();
         if (with_failureless) {
             t->gotos.assign((size_t)S * 4, AC_NO_EDGE);
             t->own_off.assign((size_t)S + 1, 0);
@@ -191,8 +195,11 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
             t->own_pid.assign(n, 0);
             std::vector<uint32_t> fill(t->own_off.begin(), t->own_off.end() - 1);
             for (uint32_t p = 0; p < n; ++p) t->own_pid[fill[t->pat_state[p]]++] = p;  // ids ascending per state
-            t->own_len.resize(n);
-            for (uint32_t j = 0; j < n; ++j) t->own_len[j] = lens[t->own_pid[j]];
+            t->own_ent.resize(2 * (size_t)n);
+            for (uint32_t j = 0; j < n; ++j) {
+                t->own_ent[2 * j] = t->own_pid[j];
+                t->own_ent[2 * j + 1] = lens[t->own_pid[j]];
+            }
             for (uint32_t i = 0; i < S; ++i) {
                 const uint32_t s = order[i];
                 for (int c = 0; c < 4; ++c) {

@@ -1,6 +1,8 @@
 // ac_internal.h - shared between the translation units of libac.so only.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -23,7 +25,7 @@ struct HostTables {
     std::vector<uint32_t> out_off;    // [S+1]
     std::vector<uint32_t> out_pid;    // [E]
     std::vector<uint32_t> pat_len;    // [P]
-    std::vector<uint32_t> out_len;    // [E] pat_len[out_pid[k]]
+    std::vector<uint32_t> out_ent;    // [2E] {out_pid[k], pat_len[out_pid[k]]}: the device's output entries
     std::vector<uint32_t> pat_state;  // [P]
     std::vector<uint32_t> depth;      // [S]
     std::vector<uint32_t> fail;       // [S]
@@ -31,7 +33,7 @@ struct HostTables {
     std::vector<uint32_t> gotos;      // [S*4] child | AC_FLAG (child has own keywords), or AC_NO_EDGE
     std::vector<uint32_t> own_off;    // [S+1]
     std::vector<uint32_t> own_pid;    // [P]
-    std::vector<uint32_t> own_len;    // [P] pat_len[own_pid[j]]
+    std::vector<uint32_t> own_ent;    // [2P] {own_pid[j], pat_len[own_pid[j]]}
 };
 static constexpr uint32_t AC_NO_EDGE = 0x7fffffffu;
 
@@ -48,12 +50,10 @@ struct ac_dfa {
     uint32_t* d_delta = nullptr;
     uint32_t* d_delta2 = nullptr;  // null when the two-base table was not built
     uint32_t* d_out_off = nullptr;
-    uint32_t* d_out_pid = nullptr;
-    uint32_t* d_out_len = nullptr;  // [E] keyword length of each output entry
+    uint32_t* d_out_ent = nullptr;  // [2E] {keyword id, keyword length} per output entry
     uint32_t* d_gotos = nullptr;    // failure-less form (null unless built)
     uint32_t* d_own_off = nullptr;
-    uint32_t* d_own_pid = nullptr;
-    uint32_t* d_own_len = nullptr;
+    uint32_t* d_own_ent = nullptr;  // [2P] {keyword id, keyword length} per own entry
     uint64_t device_bytes = 0;
     double build_ms = 0.0;
 };
@@ -85,8 +85,7 @@ struct ScanArgs {
     const uint32_t* delta2;  // two-base table (stride 2 only)
     uint32_t s2_rows;        // states with a two-base row
     const uint32_t* out_off;
-    const uint32_t* out_pid;
-    const uint32_t* out_len;  // keyword length of each out_pid entry
+    const uint2* out_ent;   // {keyword id, keyword length} per output entry
     uint32_t n_states;
     const uint32_t* text;   // packed words (16-byte aligned)
     uint64_t n;             // bases in the text
@@ -104,7 +103,7 @@ struct ScanArgs {
 int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold,
                    unsigned long long* bad, void* stream);
 int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream);
-int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,
+int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_states,
                      const unsigned long long* hits, unsigned long long* counts, void* stream);
 // Copies n packed bases from base src_off of src to base dst_off of dst.
 int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
@@ -132,8 +131,7 @@ struct BatchArgs {
     const uint32_t* delta2;
     uint32_t s2_rows;
     const uint32_t* out_off;
-    const uint32_t* out_pid;
-    const uint32_t* out_len;  // keyword length of each out_pid entry
+    const uint2* out_ent;   // {keyword id, keyword length} per output entry
     uint32_t n_states;
     const BatchText* texts;         // [T] device
     const unsigned long long* item_prefix;  // [T+1] device: first work item of each text
@@ -152,8 +150,7 @@ int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream);
 struct PartDesc {
     const uint32_t* delta;     // [S*4], all rows staged in shared memory
     const uint32_t* out_off;
-    const uint32_t* out_pid;   // local ids
-    const uint32_t* out_len;
+    const uint2* out_ent;      // {local keyword id, keyword length}
     unsigned long long* hits;  // [S] slice of the shared hit buffer
     uint32_t n_states;
     uint32_t pid_offset;       // first keyword id of the chunk
@@ -177,8 +174,7 @@ static constexpr uint32_t AC_STATE_MASK31 = 0x7fffffffu;
 struct FlArgs {
     const uint32_t* gotos;    // [S*4] trie edges (AC_NO_EDGE where none), bit 31 = child has own keywords
     const uint32_t* own_off;  // [S+1]
-    const uint32_t* own_pid;  // [P]
-    const uint32_t* own_len;  // [P] keyword length of each own_pid entry
+    const uint2* own_ent;     // [P] {keyword id, keyword length}
     const uint32_t* text;
     uint64_t n;
     uint64_t own_begin, own_end;

@@ -7,9 +7,9 @@
 //   delta2   uint32[S][16]  row s = the 16 two-base transitions (64 B);
 //                           bit 31 "final state has output", bit 30 "state
 //                           after the first base has output"
-//   out_off  uint32[S+1], out_pid uint32[E]: output(s) as CSR
-//   out_len  uint32[E]     keyword length of each out_pid entry (one load
-//                          gives the start position of an occurrence)
+//   out_off  uint32[S+1], out_ent uint2[E]: output(s) as CSR, each entry
+//                          {keyword id, keyword length} (one 8-byte load gives
+//                          an occurrence's id and start position)
 //   text     uint32[ceil(n/16)] 2-bit packed, base j in bits 2*(j%16) of word j/16
 //
 // Work decomposition (the GPU form of the paper's "approach 1", Sec. IV.A):
@@ -34,8 +34,10 @@
 // The warp votes; flagged, owned positions are appended to a per-warp event
 // queue in shared memory (ballot + popc); full queues are expanded 32 events
 // at a time (warp prefix sum, one atomicAdd on the occurrence counter per 32
-// events, 16-byte streaming stores). A per-state hit counter feeds the exact
-// per-keyword counts (kept exact on overflow).
+// events) one occurrence per lane: consecutive lanes read consecutive
+// output entries and write consecutive 16-byte occurrences (streaming
+// stores). A per-state hit counter feeds the exact per-keyword counts (kept
+// exact on overflow).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -91,8 +93,7 @@ struct Tables {
     const uint32_t* __restrict__ delta2;
     uint32_t s2_rows;  // states [0, s2_rows) have two-base rows
     const uint32_t* __restrict__ out_off;
-    const uint32_t* __restrict__ out_pid;
-    const uint32_t* __restrict__ out_len;  // keyword length of each out_pid entry
+    const uint2* __restrict__ out_ent;  // {keyword id, keyword length} per output entry
 };
 
 struct Sink {
@@ -134,16 +135,24 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane
 }
 
 // Expands the n <= QCAP queued hits of this warp; called by all 32 lanes
-// together. Lane l takes events l, l + 32, ..., so every dependent step - the
-// first-base lookup, the output-set bounds, the keyword id/length and the
-// occurrence-counter atomic - is one round trip for the whole queue. Lanes
-// holding the same state combine their per-state hit counts
-// (__match_any_sync) before one atomicAdd per distinct state.
-__device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink sk) {
+// together, in two phases.
+//   Per event (lane l takes events l, l + 32, ...): the first-base lookup,
+//   the output-set bounds, the per-state hit counts (lanes holding the same
+//   state combine through __match_any_sync before one atomicAdd per distinct
+//   state), a warp prefix sum of the set sizes and one atomicAdd on the
+//   occurrence counter for the whole queue.
+//   Per occurrence: the queue entries are rewritten as {end position, first
+//   output entry, text id}; round r covers occurrence slots [32r, 32r + 32),
+//   one per lane. Every queued state has output (its step was flagged), so
+//   each event owns at least one slot and the event of a slot is the number
+//   of events starting at or before it, less one: a bit per event start,
+//   OR-reduced over the warp, and a popcount. Consecutive lanes then read
+//   consecutive output entries and write consecutive occurrences.
+__device__ __noinline__ void drain(uint4* q, uint32_t n, Tables tb, Sink sk) {
     __syncwarp();
     const uint32_t lane = threadIdx.x & 31;
     uint4 ev[EPL];
-    uint32_t st[EPL], o0[EPL], k[EPL], pid0[EPL], len0[EPL], incl[EPL];
+    uint32_t st[EPL], o0[EPL], k[EPL], ex[EPL];
     bool valid[EPL];
 #pragma unroll
     for (int h = 0; h < EPL; ++h) {
@@ -162,11 +171,6 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
         k[h] = valid[h] ? __ldg(tb.out_off + st[h] + 1) - o0[h] : 0u;
     }
 #pragma unroll
-    for (int h = 0; h < EPL; ++h) {  // first keyword of each set: loads in flight with the atomic
-        pid0[h] = k[h] ? __ldg(tb.out_pid + o0[h]) : 0u;
-        len0[h] = k[h] ? __ldg(tb.out_len + o0[h]) : 0u;
-    }
-#pragma unroll
     for (int h = 0; h < EPL; ++h) {
         const uint32_t peers = __match_any_sync(FULL, st[h]);
         if (valid[h] && lane == (uint32_t)(__ffs(peers) - 1))
@@ -174,25 +178,45 @@ __device__ __noinline__ void drain(const uint4* q, uint32_t n, Tables tb, Sink s
     }
     uint32_t total = 0;
 #pragma unroll
-    for (int h = 0; h < EPL; ++h) {  // exclusive offsets of every event's occurrences
+    for (int h = 0; h < EPL; ++h) {  // exclusive offsets, events in queue order
         const uint32_t in = warp_inclusive_sum(k[h], lane);
-        incl[h] = in + total;
+        ex[h] = total + in - k[h];
         total += __shfl_sync(FULL, in, 31);
     }
     unsigned long long base = 0;
     if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
     base = __shfl_sync(FULL, base, 31);
 #pragma unroll
-    for (int h = 0; h < EPL; ++h) {
-        unsigned long long w = base + (incl[h] - k[h]);
-        const uint64_t end_pos = ((uint64_t)ev[h].y << 32) | ev[h].x;
-        for (uint32_t t = 0; t < k[h]; ++t, ++w) {
-            if (w >= sk.capacity) break;
-            const uint32_t pid = (t ? __ldg(tb.out_pid + o0[h] + t) : pid0[h]) + sk.pid_offset;
-            const uint64_t pos = end_pos + 1 - (t ? __ldg(tb.out_len + o0[h] + t) : len0[h]) + sk.pos_offset;
+    for (int h = 0; h < EPL; ++h)
+        if (valid[h]) q[32u * h + lane] = make_uint4(ev[h].x, ev[h].y, o0[h], ev[h].w);
+    __syncwarp();
+    const uint64_t room = sk.capacity > base ? sk.capacity - base : 0ull;
+    const uint32_t stored = (uint32_t)min((uint64_t)total, room);
+    const uint32_t rounds = (uint32_t)(((uint64_t)stored + 31) >> 5);
+    uint32_t started = 0;  // events starting before this round's first slot
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t r0 = r << 5;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int h = 0; h < EPL; ++h)
+            if (k[h] && ex[h] >= r0 && ex[h] - r0 < 32u) bits |= 1u << (ex[h] - r0);
+        const uint32_t starts = __reduce_or_sync(FULL, bits);
+        const uint32_t e = started + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;  // event of this lane's slot
+        started += __popc(starts);
+        uint32_t ex_e = 0;
+#pragma unroll
+        for (int h = 0; h < EPL; ++h) {
+            const uint32_t v = __shfl_sync(FULL, ex[h], e & 31);
+            if ((e >> 5) == (uint32_t)h) ex_e = v;
+        }
+        const uint32_t slot = r0 + lane;
+        if (slot < stored) {
+            const uint4 rec = q[e];
+            const uint2 ent = __ldg(tb.out_ent + rec.z + (slot - ex_e));
+            const uint64_t pos = ((((uint64_t)rec.y) << 32) | rec.x) + 1 - ent.y + sk.pos_offset;
             // streaming store: occurrences are written once and must not evict table rows from L2
-            __stcs(reinterpret_cast<uint4*>(sk.matches + w),
-                   make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), pid, ev[h].w));
+            __stcs(reinterpret_cast<uint4*>(sk.matches + base + slot),
+                   make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), ent.x + sk.pid_offset, rec.w));
         }
     }
     __syncwarp();
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits, a.pos_offset, 0u};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -379,7 +403,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_pid, a.out_len};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
@@ -421,7 +445,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{pd.delta, nullptr, 0u, pd.out_off, pd.out_pid, pd.out_len};
+    const Tables tb{pd.delta, nullptr, 0u, pd.out_off, pd.out_ent};
     const Sink sk{a.matches, a.capacity, a.counter, pd.hits, 0ull, pd.pid_offset};
     uint4* q = sm_rows + a.max_states + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -456,7 +480,7 @@ __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t ho
     stage_hot(sm_rows, a.gotos, hot);
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
-    const Tables tb{nullptr, nullptr, 0u, a.own_off, a.own_pid, a.own_len};
+    const Tables tb{nullptr, nullptr, 0u, a.own_off, a.own_ent};
     const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
     uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
     const uint32_t lt = lanemask_lt();
@@ -544,14 +568,14 @@ __global__ void splice_kernel(uint32_t* __restrict__ dst, uint64_t dst_off, cons
 }
 
 // counts[p] = sum over states s with p in output(s) of hits[s]
-__global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint32_t* __restrict__ out_pid,
+__global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint2* __restrict__ out_ent,
                               uint32_t n_states, const unsigned long long* __restrict__ hits,
                               unsigned long long* counts) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_states; s += stride) {
         const unsigned long long h = hits[s];
         if (!h) continue;
-        for (uint32_t k = out_off[s]; k < out_off[s + 1]; ++k) atomicAdd(&counts[out_pid[k]], h);
+        for (uint32_t k = out_off[s]; k < out_off[s + 1]; ++k) atomicAdd(&counts[out_ent[k].x], h);
     }
 }
 
@@ -787,13 +811,13 @@ int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint6
     return (int)cudaGetLastError();
 }
 
-int ac_launch_counts(const uint32_t* out_off, const uint32_t* out_pid, uint32_t n_states,
+int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_states,
                      const unsigned long long* hits, unsigned long long* counts, void* stream) {
     if (n_states == 0) return 0;
     const DeviceProps& p = ac_device_props();
     uint32_t blocks = (n_states + 255) / 256;
     const uint32_t cap = (uint32_t)p.sms * 8;
     if (blocks > cap) blocks = cap;
-    counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_pid, n_states, hits, counts);
+    counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_ent, n_states, hits, counts);
     return (int)cudaGetLastError();
 }

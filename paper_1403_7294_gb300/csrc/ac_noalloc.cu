@@ -92,8 +92,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
     a.out_off = dfa->d_out_off;
-    a.out_pid = dfa->d_out_pid;
-    a.out_len = dfa->d_out_len;
+    a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
     a.text = (const uint32_t*)text->data;
     a.n = n;
@@ -109,7 +108,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     if (ac_launch_scan(a, sh, stream) != 0) return AC_ERR_CUDA;
     if (r->counts) {
         if (cudaMemsetAsync(r->counts, 0, (size_t)h.n_patterns * 8, st) != cudaSuccess) return AC_ERR_CUDA;
-        if (ac_launch_counts(dfa->d_out_off, dfa->d_out_pid, h.n_states, hits,
+        if (ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, hits,
                              (unsigned long long*)r->counts, stream) != 0)
             return AC_ERR_CUDA;
     }
