@@ -32,7 +32,9 @@
  *   - the library owns ac_dfa and ac_server objects; the caller owns every
  *     text and result buffer it passes in and keeps it alive for the call;
  *   - an ac_dfa is immutable after ac_build, so concurrent scans of one
- *     ac_dfa from several host threads / streams are safe.
+ *     ac_dfa from several host threads / streams are safe;
+ *   - a text (or a streamed piece, or one text of a batch) has fewer than
+ *     2^56 bases; a longer one is refused with AC_ERR_TOO_LARGE.
  */
 #ifndef AC_H
 #define AC_H
@@ -73,8 +75,9 @@ enum ac_build_flags {
                                 can be inspected with ac_dfa_tables but not scanned          */
     AC_BUILD_NO_STRIDE2 = 4u, /* skip the two-bases-per-lookup table (saves 64 B per state of
                                 device memory; scans then always read one base per lookup)   */
-    AC_BUILD_FAILURELESS = 8u /* also keep the trie edges and per-state own keywords, for
+    AC_BUILD_FAILURELESS = 8u, /* also keep the trie edges and per-state own keywords, for
                                 ac_scan_failureless (16 B per state + 8 B per keyword)        */
+    AC_BUILD_NO_STRIDE3 = 16u /* skip the three-bases-per-lookup table (256 B per row)          */
 };
 
 typedef struct {
@@ -82,6 +85,9 @@ typedef struct {
     uint32_t stride2_states; /* rows of the two-base table: the first (breadth-first, i.e.
                                 shallowest) this many states; 0 = min(S, 2^19). Steps from
                                 deeper states take two one-base lookups instead.          */
+    uint32_t stride3_states; /* rows of the three-base table, likewise; 0 = min(S, 2^17);
+                                at most 2^22. Three-base steps from deeper states take a
+                                two-base and a one-base lookup (or three one-base ones).  */
 } ac_build_opts;
 
 /*
@@ -95,7 +101,9 @@ typedef struct {
  * (so shallow, frequently visited states have small ids). Unless
  * AC_BUILD_NO_STRIDE2 is set it also builds delta2[s][x | y<<2] =
  * delta[delta[s][x]][y] for the shallowest opts->stride2_states states, which
- * lets a scan read two bases per lookup. Unless AC_BUILD_HOST_ONLY is set the
+ * lets a scan read two bases per lookup, and unless AC_BUILD_NO_STRIDE3 is set
+ * delta3[s][x | y<<2 | z<<4] (three bases) for the shallowest
+ * opts->stride3_states states. Unless AC_BUILD_HOST_ONLY is set the
  * tables are copied to the current device (synchronously) and the dfa is
  * ready to scan.
  * Errors: AC_ERR_INVALID_ARG (NULL pointers, n_patterns == 0),
@@ -120,6 +128,7 @@ typedef struct {
     uint64_t device_bytes; /* all device memory held by the dfa                   */
     double build_ms;       /* host time of the build (construction + upload)      */
     uint64_t table2_bytes; /* 64 * rows of the two-base table, 0 if not built     */
+    uint64_t table3_bytes; /* 256 * rows of the three-base table, 0 if not built  */
 } ac_dfa_info_t;
 
 int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
@@ -135,7 +144,11 @@ int ac_dfa_info(const ac_dfa* dfa, ac_dfa_info_t* out);
  *   delta2[16*s + (x | y<<2)] for s < table2_bytes/64 (NULL if not built):
  *                   bits 0-29 the state after bases x then y, bit 31 set when
  *                   that state has output, bit 30 set when the state after x
- *                   alone has output. */
+ *                   alone has output;
+ *   delta3[64*s + (x | y<<2 | z<<4)] for s < table3_bytes/256 (NULL if not
+ *                   built): bits 0-28 the state after bases x, y, z; bits 31,
+ *                   30 and 29 set when the states after z, after y and after x
+ *                   have output. */
 typedef struct {
     const uint32_t* delta;
     const uint32_t* out_off;
@@ -152,6 +165,7 @@ typedef struct {
     const uint32_t* gotos;
     const uint32_t* own_off;
     const uint32_t* own_pid;
+    const uint32_t* delta3;
 } ac_dfa_tables_t;
 
 int ac_dfa_tables(const ac_dfa* dfa, ac_dfa_tables_t* out);
@@ -209,7 +223,7 @@ typedef struct {
     uint32_t flags;       /* ac_scan_flags                                      */
     uint32_t text_id;     /* copied into every ac_match.text_id (ac_scan only)  */
     uint32_t stride;      /* bases per table lookup: 1, 2 (needs the two-base
-                             table), or 0 = tuned                              */
+                             table), 3 (needs the three-base table), or 0 = tuned */
     uint32_t reserved;
 } ac_scan_opts;
 
@@ -243,11 +257,17 @@ int ac_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, uint32_t flags, 
  * Writes min(n_matches, capacity) occurrences to result->matches (any order)
  * and, if result->counts != NULL, the exact per-keyword counts. Texts and
  * results may be on the host or the device (flags in ac_text / ac_result);
- * host data is staged through stream-ordered device memory.
+ * host data is staged through stream-ordered device memory. When the text
+ * and the results are both on the host, stats is NULL and the owned range
+ * has at least 512 Mbase, the range is scanned in 256 Mbase pieces whose
+ * host-to-device and device-to-host copies (on two library-owned streams,
+ * ordered against `stream` by events) overlap the scans of neighbouring
+ * pieces; the results are the same.
  * Synchronises `stream` once (to learn n_matches).
  * Errors: AC_ERR_INVALID_ARG, AC_ERR_NO_DEVICE, AC_ERR_ALPHABET (with
  * bad_offset), AC_ERR_OVERFLOW (n_matches and counts exact; retry with
- * capacity >= n_matches), AC_ERR_OOM, AC_ERR_CUDA.
+ * capacity >= n_matches), AC_ERR_TOO_LARGE (2^56 bases or more), AC_ERR_OOM,
+ * AC_ERR_CUDA.
  * stats (nullable) receives the launch shape and device times.
  */
 int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* result, const ac_scan_opts* opts /* nullable */,

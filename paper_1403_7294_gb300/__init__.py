@@ -58,15 +58,15 @@ class Dfa:
     """A built machine (ac_build). Immutable; freed with close() or on GC."""
 
     def __init__(self, patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True,
-                 stride2_states: int = 0, failureless: bool = False):
+                 stride2_states: int = 0, failureless: bool = False, stride3: bool = True, stride3_states: int = 0):
         L = lib()
         self._bufs = [_as_bytes(p) for p in patterns]
         n = len(self._bufs)
         ptrs = (ctypes.c_char_p * max(n, 1))(*self._bufs)
         lens = np.array([len(b) for b in self._bufs], dtype=np.uint32)
         opts = N.BuildOpts((N.AC_BUILD_FOLD_CASE if fold_case else 0) | (N.AC_BUILD_HOST_ONLY if host_only else 0)
-                           | (0 if stride2 else N.AC_BUILD_NO_STRIDE2) | (N.AC_BUILD_FAILURELESS if failureless else 0),
-                           stride2_states)
+                           | (0 if stride2 else N.AC_BUILD_NO_STRIDE2) | (N.AC_BUILD_FAILURELESS if failureless else 0)
+                           | (0 if stride3 else N.AC_BUILD_NO_STRIDE3), stride2_states, stride3_states)
         h = ctypes.c_void_p()
         N.check(L.ac_build(ctypes.cast(ptrs, ctypes.c_void_p), lens.ctypes.data, n, ctypes.byref(opts),
                            ctypes.byref(h)), "ac_build")
@@ -91,7 +91,7 @@ class Dfa:
         N.check(lib().ac_dfa_tables(self.h, ctypes.byref(t)), "ac_dfa_tables")
         S, Pn, E = self.info["n_states"], self.info["n_patterns"], self.info["out_entries"]
         sizes = {"delta": 4 * S, "out_off": S + 1, "out_pid": E, "pat_len": Pn, "pat_state": Pn, "depth": S, "fail": S,
-                 "delta2": self.info["table2_bytes"] // 4}
+                 "delta2": self.info["table2_bytes"] // 4, "delta3": self.info["table3_bytes"] // 4}
         if t.gotos:  # failure-less form
             sizes.update({"gotos": 4 * S, "own_off": S + 1, "own_pid": Pn})
         return {k: np.ctypeslib.as_array(getattr(t, k), shape=(v,)).copy() if v else np.zeros(0, np.uint32)
@@ -110,9 +110,9 @@ class Dfa:
 
 
 def build(patterns: Sequence, fold_case: bool = False, host_only: bool = False, stride2: bool = True,
-          stride2_states: int = 0, failureless: bool = False) -> Dfa:
+          stride2_states: int = 0, failureless: bool = False, stride3: bool = True, stride3_states: int = 0) -> Dfa:
     return Dfa(patterns, fold_case=fold_case, host_only=host_only, stride2=stride2, stride2_states=stride2_states,
-               failureless=failureless)
+               failureless=failureless, stride3=stride3, stride3_states=stride3_states)
 
 
 # ------------------------------------------------------------------- texts
@@ -344,7 +344,7 @@ class PartSet:
         n = len(bufs)
         ptrs = (ctypes.c_char_p * max(n, 1))(*bufs)
         lens = np.array([len(b) for b in bufs], dtype=np.uint32)
-        opts = N.BuildOpts(N.AC_BUILD_FOLD_CASE if fold_case else 0, 0)
+        opts = N.BuildOpts(N.AC_BUILD_FOLD_CASE if fold_case else 0, 0, 0)
         h = ctypes.c_void_p()
         N.check(lib().ac_build_partitioned(ctypes.cast(ptrs, ctypes.c_void_p), lens.ctypes.data, n, max_states,
                                            ctypes.byref(opts), ctypes.byref(h)), "ac_build_partitioned")

@@ -29,6 +29,7 @@ AC_BUILD_FOLD_CASE = 1
 AC_BUILD_HOST_ONLY = 2
 AC_BUILD_NO_STRIDE2 = 4
 AC_BUILD_FAILURELESS = 8
+AC_BUILD_NO_STRIDE3 = 16
 AC_TEXT_ASCII = 0
 AC_TEXT_PACKED2 = 1
 AC_SCAN_FOLD_CASE = 1
@@ -39,21 +40,21 @@ P = ctypes.c_void_p
 
 
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("flags", u32), ("stride2_states", u32)]
+    _fields_ = [("flags", u32), ("stride2_states", u32), ("stride3_states", u32)]
 
 
 class DfaInfo(ctypes.Structure):
     _fields_ = [
         ("n_states", u32), ("n_patterns", u32), ("max_len", u32), ("min_len", u32),
         ("max_depth", u32), ("on_device", u32), ("table_bytes", u64), ("out_entries", u64),
-        ("device_bytes", u64), ("build_ms", ctypes.c_double), ("table2_bytes", u64),
+        ("device_bytes", u64), ("build_ms", ctypes.c_double), ("table2_bytes", u64), ("table3_bytes", u64),
     ]
 
 
 class DfaTables(ctypes.Structure):
     _fields_ = [(k, ctypes.POINTER(u32))
                 for k in ("delta", "out_off", "out_pid", "pat_len", "pat_state", "depth", "fail", "delta2", "gotos",
-                          "own_off", "own_pid")]
+                          "own_off", "own_pid", "delta3")]
 
 
 class Text(ctypes.Structure):

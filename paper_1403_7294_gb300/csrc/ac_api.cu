@@ -151,6 +151,7 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
     if (!d) return AC_ERR_OOM;
     int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0,
                            (flags & AC_BUILD_NO_STRIDE2) == 0, opts ? opts->stride2_states : 0u,
+                           (flags & AC_BUILD_NO_STRIDE3) == 0, opts ? opts->stride3_states : 0u,
                            (flags & AC_BUILD_FAILURELESS) != 0, &d->host, nullptr);
     if (rc != AC_OK) {
         delete d;
@@ -164,11 +165,12 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
             const std::vector<uint32_t>* src;
         } ups[] = {{&d->d_delta, &h.delta},   {&d->d_out_off, &h.out_off}, {&d->d_out_ent, &h.out_ent},
                    {&d->d_delta2, &h.delta2}, {&d->d_gotos, &h.gotos},     {&d->d_own_off, &h.own_off},
-                   {&d->d_own_ent, &h.own_ent}};
+                   {&d->d_own_ent, &h.own_ent}, {&d->d_delta3, &h.delta3}};
         cudaError_t e = cudaSuccess;
         for (auto& u : ups) {
             const bool optional =
-                u.dst == &d->d_delta2 || u.dst == &d->d_gotos || u.dst == &d->d_own_off || u.dst == &d->d_own_ent;
+                u.dst == &d->d_delta2 || u.dst == &d->d_gotos || u.dst == &d->d_own_off || u.dst == &d->d_own_ent ||
+                u.dst == &d->d_delta3;
             if (optional && u.src->empty()) continue;  // two-base / failure-less tables not built
             const size_t bytes = std::max<size_t>(u.src->size(), 1) * sizeof(uint32_t);
             e = dev_alloc((void**)u.dst, bytes);
@@ -197,6 +199,7 @@ extern "C" void ac_free(ac_dfa* d) {
         cudaDeviceSynchronize();
         cudaFree(d->d_delta);
         cudaFree(d->d_delta2);
+        cudaFree(d->d_delta3);
         cudaFree(d->d_out_off);
         cudaFree(d->d_out_ent);
         cudaFree(d->d_gotos);
@@ -221,6 +224,7 @@ extern "C" int ac_dfa_info(const ac_dfa* d, ac_dfa_info_t* o) {
     o->device_bytes = d->device_bytes;
     o->build_ms = d->build_ms;
     o->table2_bytes = (uint64_t)h.s2_rows * 64;
+    o->table3_bytes = (uint64_t)h.s3_rows * 256;
     return AC_OK;
 }
 
@@ -235,6 +239,7 @@ extern "C" int ac_dfa_tables(const ac_dfa* d, ac_dfa_tables_t* o) {
     o->depth = h.depth.data();
     o->fail = h.fail.data();
     o->delta2 = h.delta2.empty() ? nullptr : h.delta2.data();
+    o->delta3 = h.delta3.empty() ? nullptr : h.delta3.data();
     o->gotos = h.gotos.empty() ? nullptr : h.gotos.data();
     o->own_off = h.own_off.empty() ? nullptr : h.own_off.data();
     o->own_pid = h.own_pid.empty() ? nullptr : h.own_pid.data();
@@ -289,14 +294,17 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     // built-in default (measured best on the benchmark workloads when untuned):
     // one chain per thread, 1024 threads, half of the shared memory for states
     if (!sh.interleave) sh.interleave = 1;
-    if (!sh.stride || !dfa->d_delta2) sh.stride = 1;
+    if (sh.stride == 3 && !dfa->d_delta3) sh.stride = 2;
+    if (!sh.stride || (sh.stride == 2 && !dfa->d_delta2)) sh.stride = 1;
     if (sh.stride == 2 && sh.interleave > 4) sh.interleave = 4;
-    if (!sh.threads) sh.threads = ac_max_threads(sh.interleave);
-    sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave));
+    if (sh.stride == 3 && sh.interleave > 2) sh.interleave = 2;
+    if (!sh.threads) sh.threads = ac_max_threads(sh.interleave, sh.stride);
+    sh.threads = std::min(sh.threads, ac_max_threads(sh.interleave, sh.stride));
     const uint32_t max_hot = ac_max_hot_states(sh.threads, sh.stride);
     if (!(o && o->hot_states >= 0) && !sh.hot && !tuned_hot_set) sh.hot = std::min(h.n_states, max_hot / 2);
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
     if (sh.stride == 2) sh.hot = std::min(sh.hot, h.s2_rows);  // staged from the two-base rows
+    if (sh.stride == 3) sh.hot = std::min(sh.hot, h.s3_rows);  // staged from the three-base rows
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
     const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
     if (!sh.chunk) {
@@ -322,7 +330,7 @@ bool valid_shape_opts(const ac_scan_opts* o) {
     if (o->interleave && o->interleave != 1 && o->interleave != 2 && o->interleave != 4 && o->interleave != 8)
         return false;
     if (o->threads && o->threads > ac_max_threads(o->interleave ? o->interleave : 1)) return false;
-    if (o->stride > 2 || (o->stride == 2 && o->interleave == 8)) return false;
+    if (o->stride > 3 || (o->stride == 2 && o->interleave == 8) || (o->stride == 3 && o->interleave > 2)) return false;
     return true;
 }
 
@@ -424,6 +432,8 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
+    a.delta3 = dfa->d_delta3;
+    a.s3_rows = h.s3_rows;
     a.out_off = dfa->d_out_off;
     a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
@@ -513,9 +523,11 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
-    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
+    if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
+        return AC_ERR_INVALID_ARG;
     const uint64_t n = text->n_bases;
     const uint64_t own_begin = opts ? opts->range_begin : 0;
     const uint64_t own_end = (opts && opts->range_end) ? opts->range_end : n;
@@ -692,6 +704,8 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
         sa.delta = dfa->d_delta;
         sa.delta2 = dfa->d_delta2;
         sa.s2_rows = h.s2_rows;
+        sa.delta3 = dfa->d_delta3;
+        sa.s3_rows = h.s3_rows;
         sa.out_off = dfa->d_out_off;
         sa.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
         sa.n_states = h.n_states;
@@ -782,6 +796,7 @@ extern "C" int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_re
     if (!dfa->d_gotos) return AC_ERR_INVALID_ARG;  // built without AC_BUILD_FAILURELESS
     if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
         return AC_ERR_INVALID_ARG;
@@ -868,9 +883,11 @@ extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, 
     const ac_dfa* dfa = s->dfa;
     if (piece->encoding != AC_TEXT_ASCII && piece->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (piece->n_bases && !piece->data) return AC_ERR_INVALID_ARG;
+    if (piece->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
-    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
+    if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
+        return AC_ERR_INVALID_ARG;
     if (piece->on_device && piece->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(piece->data) & 15))
         return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
@@ -982,7 +999,7 @@ extern "C" int ac_build_partitioned(const char* const* patterns, const uint32_t*
     if (!s) return AC_ERR_OOM;
     s->n_patterns = n;
     ac_build_opts o{};
-    o.flags = (opts ? opts->flags : 0u) | AC_BUILD_NO_STRIDE2;
+    o.flags = (opts ? opts->flags : 0u) | AC_BUILD_NO_STRIDE2 | AC_BUILD_NO_STRIDE3;
     for (size_t i = 0; i + 1 < bounds.size(); ++i) {
         const uint32_t a = bounds[i], b = bounds[i + 1];
         if (a == b) continue;
@@ -1020,6 +1037,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
     r->bad_offset = ~0ull;
     if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
+    if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
         return AC_ERR_INVALID_ARG;
@@ -1167,7 +1185,8 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
-    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
+    if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
+        return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     const int enc = n_texts ? texts[0].encoding : AC_TEXT_PACKED2;
     const int on_dev = n_texts ? texts[0].on_device : 1;
@@ -1177,6 +1196,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
         if (t.encoding != enc || t.on_device != on_dev) return AC_ERR_INVALID_ARG;
         if (t.encoding != AC_TEXT_ASCII && t.encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
         if (t.n_bases && !t.data) return AC_ERR_INVALID_ARG;
+        if (t.n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
         if (t.on_device && t.encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(t.data) & 15))
             return AC_ERR_INVALID_ARG;
         total += t.n_bases;
@@ -1266,6 +1286,8 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
+    a.delta3 = dfa->d_delta3;
+    a.s3_rows = h.s3_rows;
     a.out_off = dfa->d_out_off;
     a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;
@@ -1344,7 +1366,8 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (!r->on_device || (r->capacity && !r->matches)) return AC_ERR_INVALID_ARG;
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
-    if (opts && opts->stride == 2 && !dfa->d_delta2) return AC_ERR_INVALID_ARG;
+    if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
+        return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     std::vector<BatchText> bt(n_texts);
     std::vector<uint64_t> lens(n_texts);
@@ -1353,6 +1376,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
         const ac_text& t = texts[i];
         if (t.encoding != AC_TEXT_PACKED2 || !t.on_device) return AC_ERR_INVALID_ARG;
         if ((t.n_bases && !t.data) || (reinterpret_cast<uintptr_t>(t.data) & 15)) return AC_ERR_INVALID_ARG;
+        if (t.n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
         bt[i] = BatchText{(const uint32_t*)t.data, t.n_bases};
         lens[i] = t.n_bases;
         total += t.n_bases;
@@ -1388,6 +1412,8 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
+    a.delta3 = dfa->d_delta3;
+    a.s3_rows = h.s3_rows;
     a.out_off = dfa->d_out_off;
     a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;

@@ -11,6 +11,8 @@
 // stride 2: delta2(s, xy) = delta(delta(s, x), y) for the 16 base pairs, with
 //          one flag for each of the two states entered (a scan that reads two
 //          bases per lookup must still report keywords ending at the first).
+// stride 3: delta3(s, xyz) = delta(delta(delta(s, x), y), z) for the 64 base
+//          triples, with one flag for each of the three states entered.
 // flatten: delta(s, a) = goto(s, a) if the edge exists, else delta(fail(s), a)
 //          (the root's missing edges loop to the root). Computed breadth
 //          first, so delta(fail(s), .) is final before s is visited. A scan
@@ -44,8 +46,8 @@ inline int base_code(uint8_t c, bool fold) {
 }  // namespace
 
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, uint32_t stride2_states, bool with_failureless, HostTables* t,
-                  uint32_t* bad_pattern) {
+                  bool with_stride2, uint32_t stride2_states, bool with_stride3, uint32_t stride3_states,
+                  bool with_failureless, HostTables* t, uint32_t* bad_pattern) {
     if (!patterns || !lens || n == 0 || !t) return AC_ERR_INVALID_ARG;
     uint64_t total = 0;
     for (uint32_t p = 0; p < n; ++p) {
@@ -227,6 +229,30 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
                         const uint32_t f = t->delta[(size_t)m * 4 + y] & AC_STATE_MASK;
                         t->delta2[(size_t)s * 16 + (x | (y << 2))] =
                             f | (has_out(f) ? AC_FLAG : 0u) | (has_out(m) ? AC_FLAG_MID : 0u);
+                    }
+                }
+        }
+
+        // ---- three bases per lookup: delta3[s][x | y << 2 | z << 4], bits 0-28 the
+        // state after z; bits 31 / 30 / 29 = the states after z / y / x have output
+        t->delta3.clear();
+        t->s3_rows = 0;
+        if (with_stride3) {
+            const uint32_t rows = std::min<uint32_t>(S, stride3_states ? stride3_states : AC_DEFAULT_STRIDE3_ROWS);
+            t->s3_rows = std::min<uint32_t>(rows, AC_MAX_STATES_STRIDE3);
+            t->delta3.assign((size_t)t->s3_rows * 64, 0);
+            auto has_out = [&](uint32_t u) { return t->out_off[u + 1] > t->out_off[u]; };
+            for (uint32_t s = 0; s < t->s3_rows; ++s)
+                for (uint32_t x = 0; x < 4; ++x) {
+                    const uint32_t a = t->delta[(size_t)s * 4 + x] & AC_STATE_MASK;
+                    for (uint32_t y = 0; y < 4; ++y) {
+                        const uint32_t b = t->delta[(size_t)a * 4 + y] & AC_STATE_MASK;
+                        for (uint32_t z = 0; z < 4; ++z) {
+                            const uint32_t c = t->delta[(size_t)b * 4 + z] & AC_STATE_MASK;
+                            t->delta3[(size_t)s * 64 + (x | (y << 2) | (z << 4))] =
+                                c | (has_out(c) ? AC_FLAG : 0u) | (has_out(b) ? AC_FLAG_MID : 0u) |
+                                (has_out(a) ? AC_FLAG_MID1 : 0u);
+                        }
                     }
                 }
         }

@@ -16,12 +16,23 @@ static constexpr uint32_t AC_STATE_MASK = 0x3fffffffu;
 static constexpr uint32_t AC_MAX_STATES = 1u << 27;          // 16 B rows stay below 2 GiB
 static constexpr uint32_t AC_MAX_STATES_STRIDE2 = 1u << 24;  // 64 B rows stay below 1 GiB
 static constexpr uint32_t AC_DEFAULT_STRIDE2_ROWS = 1u << 19;  // 32 MiB of two-base rows
+// Three-base table: bit 29 "the state after the first base has output", bit
+// 30 "after the second", bit 31 "after the third"; the state in bits 0-28.
+static constexpr uint32_t AC_FLAG_MID1 = 0x20000000u;
+static constexpr uint32_t AC_STATE_MASK3 = 0x1fffffffu;
+static constexpr uint32_t AC_DEFAULT_STRIDE3_ROWS = 1u << 17;  // 32 MiB of three-base rows
+static constexpr uint32_t AC_MAX_STATES_STRIDE3 = 1u << 22;    // 256 B rows stay at 1 GiB
+// Texts are shorter than 2^56 bases: a queued hit keeps its end position in
+// 56 bits and a tag in the top byte.
+static constexpr uint64_t AC_MAX_BASES = 1ull << 56;
 
 struct HostTables {
     uint32_t n_states = 0, n_patterns = 0, max_len = 0, min_len = 0, max_depth = 0;
     std::vector<uint32_t> delta;      // [S*4]
     std::vector<uint32_t> delta2;     // [s2_rows*16] two bases per lookup (empty if not built)
     uint32_t s2_rows = 0;             // states [0, s2_rows) have two-base rows
+    std::vector<uint32_t> delta3;     // [s3_rows*64] three bases per lookup (empty if not built)
+    uint32_t s3_rows = 0;             // states [0, s3_rows) have three-base rows
     std::vector<uint32_t> out_off;    // [S+1]
     std::vector<uint32_t> out_pid;    // [E]
     std::vector<uint32_t> pat_len;    // [P]
@@ -39,8 +50,8 @@ static constexpr uint32_t AC_NO_EDGE = 0x7fffffffu;
 
 // Builds the flattened machine on the host. Returns an ac_status.
 int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n, bool fold_case,
-                  bool with_stride2, uint32_t stride2_states, bool with_failureless, HostTables* t,
-                  uint32_t* bad_pattern);
+                  bool with_stride2, uint32_t stride2_states, bool with_stride3, uint32_t stride3_states,
+                  bool with_failureless, HostTables* t, uint32_t* bad_pattern);
 
 struct ac_dfa {
     HostTables host;
@@ -49,6 +60,7 @@ struct ac_dfa {
     // device tables
     uint32_t* d_delta = nullptr;
     uint32_t* d_delta2 = nullptr;  // null when the two-base table was not built
+    uint32_t* d_delta3 = nullptr;  // null when the three-base table was not built
     uint32_t* d_out_off = nullptr;
     uint32_t* d_out_ent = nullptr;  // [2E] {keyword id, keyword length} per output entry
     uint32_t* d_gotos = nullptr;    // failure-less form (null unless built)
@@ -61,7 +73,7 @@ struct ac_dfa {
 // ------------------------------------------------------------ launch shapes
 
 struct ScanShape {
-    uint32_t stride = 0;      // bases per lookup: 1 or 2
+    uint32_t stride = 0;      // bases per lookup: 1, 2 or 3
     uint32_t chunk = 0;       // owned bases per chunk
     uint32_t threads = 0;     // per block
     uint32_t interleave = 0;  // chunks per thread
@@ -82,8 +94,10 @@ const DeviceProps& ac_device_props();
 // Kernel launchers (ac_kernels.cu). All return cudaError_t as int.
 struct ScanArgs {
     const uint32_t* delta;
-    const uint32_t* delta2;  // two-base table (stride 2 only)
+    const uint32_t* delta2;  // two-base table (stride 2 and 3)
     uint32_t s2_rows;        // states with a two-base row
+    const uint32_t* delta3;  // three-base table (stride 3 only)
+    uint32_t s3_rows;        // states with a three-base row
     const uint32_t* out_off;
     const uint2* out_ent;   // {keyword id, keyword length} per output entry
     uint32_t n_states;
@@ -108,8 +122,9 @@ int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_s
 // Copies n packed bases from base src_off of src to base dst_off of dst.
 int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
                      void* stream);
-// Largest block size the kernels are compiled for at a given interleave.
-uint32_t ac_max_threads(uint32_t interleave);
+// Largest block size the kernels are compiled for at a given interleave and
+// stride (0 counts as 1).
+uint32_t ac_max_threads(uint32_t interleave, uint32_t stride = 1);
 // Whether kernels exist for an (interleave, stride) pair.
 bool ac_shape_compiled(uint32_t interleave, uint32_t stride);
 // Largest number of states a scan block of `threads` threads can stage in
@@ -130,6 +145,8 @@ struct BatchArgs {
     const uint32_t* delta;
     const uint32_t* delta2;
     uint32_t s2_rows;
+    const uint32_t* delta3;
+    uint32_t s3_rows;
     const uint32_t* out_off;
     const uint2* out_ent;   // {keyword id, keyword length} per output entry
     uint32_t n_states;

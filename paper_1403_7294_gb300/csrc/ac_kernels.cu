@@ -88,16 +88,24 @@ __device__ __forceinline__ uint4 load_block(const uint32_t* text, uint64_t w, ui
     return v;
 }
 
+// What the walk reads at every step.
 struct Tables {
     const uint32_t* __restrict__ delta;
     const uint32_t* __restrict__ delta2;
     uint32_t s2_rows;  // states [0, s2_rows) have two-base rows
-    const uint32_t* __restrict__ out_off;
-    const uint2* __restrict__ out_ent;  // {keyword id, keyword length} per output entry
+    const uint32_t* __restrict__ delta3;
+    uint32_t s3_rows;  // states [0, s3_rows) have three-base rows
 };
 
-struct Sink {
-    ac_match* __restrict__ matches;
+// What drain() reads: one copy per block in shared memory, so the walk keeps
+// none of these pointers in registers.
+struct Emit {
+    const uint32_t* delta;
+    const uint32_t* delta2;
+    uint32_t s2_rows;
+    const uint32_t* out_off;
+    const uint2* out_ent;  // {keyword id, keyword length} per output entry
+    ac_match* matches;
     uint64_t capacity;
     unsigned long long* counter;
     unsigned long long* hits;
@@ -106,18 +114,20 @@ struct Sink {
 };
 
 // Hits wait in a per-warp queue in shared memory, 16 B per event:
-// {end position lo, end position hi, state, text id}. Appending costs a
-// ballot and a popc; the queue is expanded into occurrences QCAP events at
-// a time, so the global occurrence counter sees one atomicAdd per QCAP hits.
-// A hit at the first base of a two-base step is queued as the state before
-// the step plus that base (EV_MID set); the drain resolves it with one
-// delta lookup, so the walk itself never waits for it.
+// {end position bits 0-31, end position bits 32-55 | tag << 24, state, text
+// id}. The tag gives the bases still to be read after `state` to reach the
+// state whose output is reported: none (tag 0), or - for a keyword that
+// ends inside a multi-base step - the step's first one or two bases (tag
+// bits 0-1 the count, bits 2-3 and 4-5 the bases), queued with the state
+// before the step; the drain resolves those with table lookups, so the walk
+// never waits for them. Appending costs a ballot and a popc; the queue is
+// expanded QCAP events at a time, so the occurrence counter sees one
+// atomicAdd per QCAP hits.
 constexpr int QCAP = 64;  // events per warp queue (larger queues make ptxas spill the walk)
 constexpr int EPL = QCAP / 32;  // events each lane expands in drain()
 static_assert(QCAP % 32 == 0, "whole events per lane");
-constexpr uint32_t EV_MID = 0x80000000u;
-constexpr uint32_t EV_BASE_SHIFT = 29;       // bits 29-30: the first base
-constexpr uint32_t EV_STATE = 0x1fffffffu;  // bits 0-28: the state (machines have < 2^27)
+__device__ __forceinline__ uint32_t tag1(uint32_t b0) { return 1u | (b0 << 2); }
+__device__ __forceinline__ uint32_t tag2(uint32_t b0, uint32_t b1) { return 2u | (b0 << 2) | (b1 << 4); }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -148,7 +158,7 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane
 //   of events starting at or before it, less one: a bit per event start,
 //   OR-reduced over the warp, and a popcount. Consecutive lanes then read
 //   consecutive output entries and write consecutive occurrences.
-__device__ __noinline__ void drain(uint4* q, uint32_t n, Tables tb, Sink sk) {
+__device__ __noinline__ void drain(uint4* q, uint32_t n, const Emit* em) {
     __syncwarp();
     const uint32_t lane = threadIdx.x & 31;
     uint4 ev[EPL];
@@ -162,19 +172,30 @@ __device__ __noinline__ void drain(uint4* q, uint32_t n, Tables tb, Sink sk) {
         st[h] = ev[h].z;
     }
 #pragma unroll
-    for (int h = 0; h < EPL; ++h)  // state after the first base of a pair: one delta lookup
-        if (valid[h] && (st[h] & EV_MID))
-            st[h] = __ldg(tb.delta + (((st[h] & EV_STATE) << 2) | ((st[h] >> EV_BASE_SHIFT) & 3u))) & AC_STATE_MASK;
+    for (int h = 0; h < EPL; ++h) {  // hits inside a multi-base step: the state after its first one or two bases
+        const uint32_t tag = ev[h].y >> 24;
+        if (valid[h] && (tag & 3u)) {
+            const uint32_t b0 = (tag >> 2) & 3u, b1 = (tag >> 4) & 3u;
+            if ((tag & 3u) == 2u && st[h] < em->s2_rows) {
+                st[h] = __ldg(em->delta2 + ((st[h] << 4) | b0 | (b1 << 2))) & AC_STATE_MASK;
+            } else {
+                st[h] = __ldg(em->delta + ((st[h] << 2) | b0)) & AC_STATE_MASK;
+                if ((tag & 3u) == 2u) st[h] = __ldg(em->delta + ((st[h] << 2) | b1)) & AC_STATE_MASK;
+            }
+        }
+    }
+    const uint32_t* __restrict__ out_off = em->out_off;
 #pragma unroll
     for (int h = 0; h < EPL; ++h) {
-        o0[h] = valid[h] ? __ldg(tb.out_off + st[h]) : 0u;
-        k[h] = valid[h] ? __ldg(tb.out_off + st[h] + 1) - o0[h] : 0u;
+        o0[h] = valid[h] ? __ldg(out_off + st[h]) : 0u;
+        k[h] = valid[h] ? __ldg(out_off + st[h] + 1) - o0[h] : 0u;
     }
+    unsigned long long* hits = em->hits;
 #pragma unroll
     for (int h = 0; h < EPL; ++h) {
         const uint32_t peers = __match_any_sync(FULL, st[h]);
         if (valid[h] && lane == (uint32_t)(__ffs(peers) - 1))
-            atomicAdd(&sk.hits[st[h]], (unsigned long long)__popc(peers));
+            atomicAdd(&hits[st[h]], (unsigned long long)__popc(peers));
     }
     uint32_t total = 0;
 #pragma unroll
@@ -184,15 +205,20 @@ __device__ __noinline__ void drain(uint4* q, uint32_t n, Tables tb, Sink sk) {
         total += __shfl_sync(FULL, in, 31);
     }
     unsigned long long base = 0;
-    if (lane == 31 && total) base = atomicAdd(sk.counter, (unsigned long long)total);
+    if (lane == 31 && total) base = atomicAdd(em->counter, (unsigned long long)total);
     base = __shfl_sync(FULL, base, 31);
 #pragma unroll
     for (int h = 0; h < EPL; ++h)
         if (valid[h]) q[32u * h + lane] = make_uint4(ev[h].x, ev[h].y, o0[h], ev[h].w);
     __syncwarp();
-    const uint64_t room = sk.capacity > base ? sk.capacity - base : 0ull;
+    const uint64_t capacity = em->capacity;
+    const uint64_t room = capacity > base ? capacity - base : 0ull;
     const uint32_t stored = (uint32_t)min((uint64_t)total, room);
     const uint32_t rounds = (uint32_t)(((uint64_t)stored + 31) >> 5);
+    const uint2* __restrict__ out_ent = em->out_ent;
+    ac_match* matches = em->matches;
+    const uint64_t pos_offset = em->pos_offset;
+    const uint32_t pid_offset = em->pid_offset;
     uint32_t started = 0;  // events starting before this round's first slot
     for (uint32_t r = 0; r < rounds; ++r) {
         const uint32_t r0 = r << 5;
@@ -212,24 +238,24 @@ __device__ __noinline__ void drain(uint4* q, uint32_t n, Tables tb, Sink sk) {
         const uint32_t slot = r0 + lane;
         if (slot < stored) {
             const uint4 rec = q[e];
-            const uint2 ent = __ldg(tb.out_ent + rec.z + (slot - ex_e));
-            const uint64_t pos = ((((uint64_t)rec.y) << 32) | rec.x) + 1 - ent.y + sk.pos_offset;
+            const uint2 ent = __ldg(out_ent + rec.z + (slot - ex_e));
+            const uint64_t pos = ((((uint64_t)(rec.y & 0xffffffu)) << 32) | rec.x) + 1 - ent.y + pos_offset;
             // streaming store: occurrences are written once and must not evict table rows from L2
-            __stcs(reinterpret_cast<uint4*>(sk.matches + base + slot),
-                   make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), ent.x + sk.pid_offset, rec.w));
+            __stcs(reinterpret_cast<uint4*>(matches + base + slot),
+                   make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), ent.x + pid_offset, rec.w));
         }
     }
     __syncwarp();
 }
 
 // Appends the hits of one ballot (mask m, this lane's flag h) to the queue.
-__device__ __forceinline__ void append(uint4* q, uint32_t& qn, uint32_t m, bool h, uint64_t end_pos, uint32_t st,
-                                       uint32_t text_id, uint32_t lt, const Tables& tb, const Sink& sk) {
+__device__ __forceinline__ void append(uint4* q, uint32_t& qn, uint32_t m, bool h, uint64_t end_pos, uint32_t tag,
+                                       uint32_t st, uint32_t text_id, uint32_t lt, const Emit* em) {
     if (qn + __popc(m) > (uint32_t)QCAP) {
-        drain(q, qn, tb, sk);
+        drain(q, qn, em);
         qn = 0;
     }
-    if (h) q[qn + __popc(m & lt)] = make_uint4((uint32_t)end_pos, (uint32_t)(end_pos >> 32), st, text_id);
+    if (h) q[qn + __popc(m & lt)] = make_uint4((uint32_t)end_pos, (uint32_t)(end_pos >> 32) | (tag << 24), st, text_id);
     qn += __popc(m);
 }
 
@@ -261,17 +287,18 @@ __device__ __forceinline__ void idle_chain(Chain& c, const uint32_t* text, uint6
     c.lo = c.hi = 0;
 }
 
-// Threads per block each interleave factor is compiled for (register budget).
-template <int I>
+// Threads per block each (interleave, stride) pair is compiled for (register
+// budget: the three-base walk holds 192 bases of text per chain).
+template <int I, int ST = 1>
 struct MaxThreads {
-    static constexpr int value = I == 1 ? 1024 : (I <= 4 ? 512 : 256);
+    static constexpr int value = I == 1 ? (ST == 3 ? 768 : 1024) : (I <= 4 ? 512 : 256);
 };
 
 // Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
 // call this together). q: this warp's event queue in shared memory.
 template <int I, int ST>
 __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
-                                     const Tables& tb, const Sink& sk, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
+                                     const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
     constexpr uint32_t ROW_SHIFT = ST == 1 ? 2 : 4;  // log2 entries per row
     constexpr uint32_t SYM_MASK = ST == 1 ? 3u : 15u;
     constexpr uint32_t FLAGS = ST == 1 ? AC_FLAG : (AC_FLAG | AC_FLAG_MID);
@@ -338,22 +365,122 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                         if (ST == 2) {  // a keyword may end at the first base of the pair
                             const bool hm = (e[j] & fmask[j] & AC_FLAG_MID) && off >= ch[j].lo && off < ch[j].hi;
                             const uint32_t mm = __ballot_sync(FULL, hm);
-                            if (mm) {
-                                const uint32_t pending =
-                                    EV_MID | (((wd[j] >> (2 * ST * k)) & 3u) << EV_BASE_SHIFT) | sp[j];
-                                append(q, qn, mm, hm, ch[j].start + off, pending, ch[j].text_id, lt, tb, sk);
-                            }
+                            if (mm)
+                                append(q, qn, mm, hm, ch[j].start + off, tag1((wd[j] >> (2 * ST * k)) & 3u), sp[j],
+                                       ch[j].text_id, lt, em);
                         }
                         const uint32_t oe = off + ST - 1;  // last base of this step
                         const bool h = (e[j] & fmask[j] & AC_FLAG) && oe >= ch[j].lo && oe < ch[j].hi;
                         const uint32_t m = __ballot_sync(FULL, h);
-                        if (m) append(q, qn, m, h, ch[j].start + oe, s[j], ch[j].text_id, lt, tb, sk);
+                        if (m) append(q, qn, m, h, ch[j].start + oe, 0u, s[j], ch[j].text_id, lt, em);
                     }
                 }
             }
         }
     }
-    if (qn) drain(q, qn, tb, sk);
+    if (qn) drain(q, qn, em);
+}
+
+// Walk I chains in lockstep three bases per lookup: the three-base row for
+// states [0, s3_rows) (from shared memory below `hot`), a two-base and a
+// one-base lookup for the states with a two-base row, three one-base lookups
+// beyond. A step's entry has one flag per base entered (bits 29, 30, 31: a
+// keyword ends after the first, second, third base). The text is loaded 192
+// bases (three 16-byte loads) at a time and consumed 48 bases (three words,
+// sixteen steps) at a time.
+template <int I>
+__device__ __forceinline__ void walk3(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
+                                      const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
+    constexpr uint32_t FLAGS = AC_FLAG | AC_FLAG_MID | AC_FLAG_MID1;
+    uint32_t nb = 0;
+#pragma unroll
+    for (int j = 0; j < I; ++j) {
+        const uint32_t b = (ch[j].hi + 191) / 192;
+        nb = b > nb ? b : nb;
+    }
+    nb = __reduce_max_sync(FULL, nb);
+    const uint32_t lt = lanemask_lt();
+    uint32_t s[I];
+#pragma unroll
+    for (int j = 0; j < I; ++j) s[j] = 0;
+    uint32_t qn = 0;  // queued events (same value in every lane)
+
+    for (uint32_t b = 0; b < nb; ++b) {
+        uint32_t w[I][12];
+        uint32_t fmask[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const bool act = 192u * b < ch[j].hi;
+            fmask[j] = act ? FLAGS : 0u;
+            const uint64_t w0 = (ch[j].start >> 4) + 12ull * b;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const uint4 x = act ? load_block(ch[j].text, w0 + 4 * v, ch[j].nwords, pol_txt) : make_uint4(0, 0, 0, 0);
+                w[j][4 * v] = x.x;
+                w[j][4 * v + 1] = x.y;
+                w[j][4 * v + 2] = x.z;
+                w[j][4 * v + 3] = x.w;
+            }
+        }
+#pragma unroll 1
+        for (uint32_t g = 0; g < 4; ++g) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int o = 6 * k, wi = o >> 5, sh = o & 31;  // the step's 6 bits within words 0-2
+                uint32_t e[I], sp[I], sy[I];
+#pragma unroll
+                for (int j = 0; j < I; ++j) {
+                    sy[j] = (sh <= 26 ? (w[j][wi] >> sh) : __funnelshift_r(w[j][wi], w[j][wi + 1], sh)) & 63u;
+                    const uint32_t cur = s[j];
+                    if (cur < tb.s3_rows) {
+                        const uint32_t idx = (cur << 6) | sy[j];
+                        e[j] = (cur < hot) ? sm[idx] : ld_table(tb.delta3 + idx, pol_tab);
+                    } else if (cur < tb.s2_rows) {  // two bases, then one
+                        const uint32_t e2 = ld_table(tb.delta2 + ((cur << 4) | (sy[j] & 15u)), pol_tab);
+                        const uint32_t e1 = ld_table(tb.delta + (((e2 & AC_STATE_MASK) << 2) | (sy[j] >> 4)), pol_tab);
+                        e[j] = (e1 & (AC_FLAG | AC_STATE_MASK3)) | ((e2 >> 1) & (AC_FLAG_MID | AC_FLAG_MID1));
+                    } else {  // deep state: three one-base lookups
+                        const uint32_t a1 = ld_table(tb.delta + ((cur << 2) | (sy[j] & 3u)), pol_tab);
+                        const uint32_t a2 =
+                            ld_table(tb.delta + (((a1 & AC_STATE_MASK) << 2) | ((sy[j] >> 2) & 3u)), pol_tab);
+                        const uint32_t a3 = ld_table(tb.delta + (((a2 & AC_STATE_MASK) << 2) | (sy[j] >> 4)), pol_tab);
+                        e[j] = (a3 & (AC_FLAG | AC_STATE_MASK3)) | ((a2 & AC_FLAG) >> 1) | ((a1 & AC_FLAG) >> 2);
+                    }
+                }
+                uint32_t any = 0;
+#pragma unroll
+                for (int j = 0; j < I; ++j) {
+                    sp[j] = s[j];
+                    s[j] = e[j] & AC_STATE_MASK3;
+                    any |= e[j] & fmask[j];
+                }
+                if (__any_sync(FULL, any)) {
+                    const uint32_t off = 192u * b + 48u * g + 3u * k;  // first base of this step
+#pragma unroll
+                    for (int j = 0; j < I; ++j) {
+                        const bool h1 = (e[j] & fmask[j] & AC_FLAG_MID1) && off >= ch[j].lo && off < ch[j].hi;
+                        const uint32_t m1 = __ballot_sync(FULL, h1);
+                        if (m1)
+                            append(q, qn, m1, h1, ch[j].start + off, tag1(sy[j] & 3u), sp[j], ch[j].text_id, lt, em);
+                        const bool h2 =
+                            (e[j] & fmask[j] & AC_FLAG_MID) && off + 1 >= ch[j].lo && off + 1 < ch[j].hi;
+                        const uint32_t m2 = __ballot_sync(FULL, h2);
+                        if (m2)
+                            append(q, qn, m2, h2, ch[j].start + off + 1, tag2(sy[j] & 3u, (sy[j] >> 2) & 3u), sp[j],
+                                   ch[j].text_id, lt, em);
+                        const bool h3 = (e[j] & fmask[j] & AC_FLAG) && off + 2 >= ch[j].lo && off + 2 < ch[j].hi;
+                        const uint32_t m3 = __ballot_sync(FULL, h3);
+                        if (m3) append(q, qn, m3, h3, ch[j].start + off + 2, 0u, s[j], ch[j].text_id, lt, em);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < I; ++j)  // the next 48 bases move to words 0-2
+#pragma unroll
+                for (int v = 0; v < 9; ++v) w[j][v] = w[j][v + 3];
+        }
+    }
+    if (qn) drain(q, qn, em);
 }
 
 // Copies `rows16` 16-byte rows (the hot prefix of the table) to shared memory.
@@ -364,15 +491,18 @@ __device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* table,
 }
 
 template <int I, int ST>
-__global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
+__global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
     extern __shared__ uint4 sm_rows[];
-    constexpr uint32_t R16 = ST == 1 ? 1 : 4;  // 16-byte units per row
-    stage_hot(sm_rows, ST == 1 ? a.delta : a.delta2, hot * R16);
+    __shared__ Emit em;
+    if (threadIdx.x == 0)
+        em = Emit{a.delta,    a.delta2,   a.s2_rows, a.out_off, a.out_ent, a.matches,
+                  a.capacity, a.counter,  a.hits,    a.pos_offset, 0u};
+    constexpr uint32_t R16 = ST == 1 ? 1 : (ST == 2 ? 4 : 16);  // 16-byte units per row
+    stage_hot(sm_rows, ST == 1 ? a.delta : (ST == 2 ? a.delta2 : a.delta3), hot * R16);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits, a.pos_offset, 0u};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,22 +519,27 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) scan_kernel(ScanArgs a, 
                 idle_chain(ch[j], a.text, nwords, a.text_id);
             }
         }
-        walk<I, ST>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
+        if constexpr (ST == 3)
+            walk3<I>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        else
+            walk<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
 // Persistent batched scan: warps take 32*I work items at a time from a
 // device cursor; item -> (text, chunk) by binary search over item_prefix.
 template <int I, int ST>
-__global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a, uint32_t hot) {
+__global__ void __launch_bounds__(MaxThreads<I, ST>::value) batch_kernel(BatchArgs a, uint32_t hot) {
     extern __shared__ uint4 sm_rows[];
-    constexpr uint32_t R16 = ST == 1 ? 1 : 4;
-    stage_hot(sm_rows, ST == 1 ? a.delta : a.delta2, hot * R16);
+    __shared__ Emit em;
+    if (threadIdx.x == 0)
+        em = Emit{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent, a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+    constexpr uint32_t R16 = ST == 1 ? 1 : (ST == 2 ? 4 : 16);
+    stage_hot(sm_rows, ST == 1 ? a.delta : (ST == 2 ? a.delta2 : a.delta3), hot * R16);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -428,7 +563,10 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
                 set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
             }
         }
-        walk<I, ST>(ch, sm, hot, tb, sk, q, pol_tab, pol_txt);
+        if constexpr (ST == 3)
+            walk3<I>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        else
+            walk<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -440,13 +578,16 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) batch_kernel(BatchArgs a
 template <int I>
 __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArgs a, uint32_t chunk, uint64_t n_chunks) {
     extern __shared__ uint4 sm_rows[];
+    __shared__ Emit em;
     const PartDesc pd = a.parts[blockIdx.y];
-    stage_hot(sm_rows, pd.delta, pd.n_states);
+    if (threadIdx.x == 0)
+        em = Emit{pd.delta, nullptr, 0u, pd.out_off, pd.out_ent, a.matches, a.capacity, a.counter, pd.hits, 0ull,
+                  pd.pid_offset};
+    stage_hot(sm_rows, pd.delta, pd.n_states);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{pd.delta, nullptr, 0u, pd.out_off, pd.out_ent};
-    const Sink sk{a.matches, a.capacity, a.counter, pd.hits, 0ull, pd.pid_offset};
+    const Tables tb{pd.delta, nullptr, 0u, nullptr, 0u};
     uint4* q = sm_rows + a.max_states + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +604,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
                 idle_chain(ch[j], a.text, nwords, 0u);
             }
         }
-        walk<I, 1>(ch, sm, pd.n_states, tb, sk, q, pol_tab, pol_txt);
+        walk<I, 1>(ch, sm, pd.n_states, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -477,11 +618,12 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
 // own-keyword tables); ownership is by end position, as in the main scan.
 __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t hot) {
     extern __shared__ uint4 sm_rows[];
-    stage_hot(sm_rows, a.gotos, hot);
+    __shared__ Emit em;  // no multi-base steps here: the drain needs no transition table
+    if (threadIdx.x == 0)
+        em = Emit{nullptr, nullptr, 0u, a.own_off, a.own_ent, a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+    stage_hot(sm_rows, a.gotos, hot);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
-    const Tables tb{nullptr, nullptr, 0u, a.own_off, a.own_ent};
-    const Sink sk{a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
     uint4* q = sm_rows + hot + (threadIdx.x >> 5) * QCAP;
     const uint32_t lt = lanemask_lt();
     const uint64_t first = a.own_begin > a.halo ? a.own_begin - a.halo : 0;  // starts whose ends can be owned
@@ -505,10 +647,10 @@ __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t ho
             if (alive) s = e & AC_STATE_MASK31;
             const bool h = alive && (e & AC_FLAG) && p >= a.own_begin && p < a.own_end;
             const uint32_t m = __ballot_sync(FULL, h);
-            if (m) append(q, qn, m, h, p, s, a.text_id, lt, tb, sk);
+            if (m) append(q, qn, m, h, p, 0u, s, a.text_id, lt, &em);
         }
     }
-    if (qn) drain(q, qn, tb, sk);
+    if (qn) drain(q, qn, &em);
 }
 
 __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint32_t* __restrict__ packed, int fold,
@@ -603,7 +745,8 @@ int set_smem(K kern, size_t bytes) {
     return rc;
 }
 
-// The (interleave, stride) pairs that are compiled: stride 2 up to interleave 4.
+// The (interleave, stride) pairs that are compiled: stride 2 up to interleave 4,
+// stride 3 up to interleave 2.
 template <typename F>
 int dispatch(uint32_t interleave, uint32_t stride, F&& f) {
     if (stride == 1) {
@@ -618,6 +761,11 @@ int dispatch(uint32_t interleave, uint32_t stride, F&& f) {
             case 1: return f.template operator()<1, 2>();
             case 2: return f.template operator()<2, 2>();
             case 4: return f.template operator()<4, 2>();
+        }
+    } else if (stride == 3) {
+        switch (interleave) {
+            case 1: return f.template operator()<1, 3>();
+            case 2: return f.template operator()<2, 3>();
         }
     }
     return -1;
@@ -646,7 +794,8 @@ const DeviceProps& ac_device_props() {
     return cache[dev];
 }
 
-uint32_t ac_max_threads(uint32_t interleave) {
+uint32_t ac_max_threads(uint32_t interleave, uint32_t stride) {
+    if (stride == 3) return interleave == 1 ? MaxThreads<1, 3>::value : (interleave == 2 ? MaxThreads<2, 3>::value : 0);
     switch (interleave) {
         case 1: return MaxThreads<1>::value;
         case 2: return MaxThreads<2>::value;
@@ -658,17 +807,25 @@ uint32_t ac_max_threads(uint32_t interleave) {
 
 bool ac_shape_compiled(uint32_t interleave, uint32_t stride) {
     return (stride == 1 && (interleave == 1 || interleave == 2 || interleave == 4 || interleave == 8)) ||
-           (stride == 2 && (interleave == 1 || interleave == 2 || interleave == 4));
+           (stride == 2 && (interleave == 1 || interleave == 2 || interleave == 4)) ||
+           (stride == 3 && (interleave == 1 || interleave == 2));
 }
 
+// Shared memory each kernel declares statically (its Emit block), kept free
+// of the dynamic allocation so the two fit the per-block limit together.
+constexpr size_t kStaticSmem = 256;
+static_assert(sizeof(Emit) <= kStaticSmem, "Emit fits the reserve");
+
+static size_t row_bytes(uint32_t stride) { return stride == 3 ? 256 : (stride == 2 ? 64 : 16); }
+
 size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads, uint32_t stride) {
-    return (size_t)hot * (stride == 2 ? 64 : 16) + (size_t)(threads / 32) * QCAP * 16;
+    return (size_t)hot * row_bytes(stride) + (size_t)(threads / 32) * QCAP * 16;
 }
 
 uint32_t ac_max_hot_states(uint32_t threads, uint32_t stride) {
     const DeviceProps& p = ac_device_props();
-    const size_t queues = ac_scan_smem_bytes(0, threads, stride);
-    return p.smem_optin > queues ? (uint32_t)((p.smem_optin - queues) / (stride == 2 ? 64 : 16)) : 0u;
+    const size_t queues = ac_scan_smem_bytes(0, threads, stride) + kStaticSmem;
+    return p.smem_optin > queues ? (uint32_t)((p.smem_optin - queues) / row_bytes(stride)) : 0u;
 }
 
 namespace {
@@ -753,7 +910,7 @@ int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold
 int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
     const uint64_t owned = a.own_end > a.own_begin ? a.own_end - a.own_begin : 0;
     if (owned == 0) return 0;
-    if (sh.stride == 2 && !a.delta2) return (int)cudaErrorInvalidValue;
+    if ((sh.stride == 2 && !a.delta2) || (sh.stride == 3 && !a.delta3)) return (int)cudaErrorInvalidValue;
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
     const int rc = dispatch(sh.interleave, sh.stride, ScanLaunch{a, sh, n_chunks, (cudaStream_t)stream});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
@@ -761,7 +918,7 @@ int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
 
 int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
     if (a.n_items == 0) return 0;
-    if (sh.stride == 2 && !a.delta2) return (int)cudaErrorInvalidValue;
+    if ((sh.stride == 2 && !a.delta2) || (sh.stride == 3 && !a.delta3)) return (int)cudaErrorInvalidValue;
     const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{a, sh, (cudaStream_t)stream, false});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }

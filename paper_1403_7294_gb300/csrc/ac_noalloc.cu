@@ -58,6 +58,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (text->encoding != AC_TEXT_PACKED2 || !text->on_device || !r->on_device) return AC_ERR_INVALID_ARG;
     if (text->n_bases && (!text->data || (reinterpret_cast<uintptr_t>(text->data) & 15))) return AC_ERR_INVALID_ARG;
+    if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
     if (opts && opts->threads && (opts->threads < 32 || opts->threads > 1024 || opts->threads % 32))
         return AC_ERR_INVALID_ARG;
@@ -91,6 +92,8 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     a.delta = dfa->d_delta;
     a.delta2 = dfa->d_delta2;
     a.s2_rows = h.s2_rows;
+    a.delta3 = dfa->d_delta3;
+    a.s3_rows = h.s3_rows;
     a.out_off = dfa->d_out_off;
     a.out_ent = reinterpret_cast<const uint2*>(dfa->d_out_ent);
     a.n_states = h.n_states;

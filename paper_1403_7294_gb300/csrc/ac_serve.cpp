@@ -351,6 +351,7 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
     if (t->on_device) return AC_ERR_INVALID_ARG;
     if (t->encoding != AC_TEXT_ASCII && t->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (t->n_bases && !t->data) return AC_ERR_INVALID_ARG;
+    if (t->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (t->encoding == AC_TEXT_ASCII) {  // reject bad input before it is queued
         const uint8_t* b = (const uint8_t*)t->data;
         for (uint64_t i = 0; i < t->n_bases; ++i)

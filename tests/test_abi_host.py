@@ -233,6 +233,86 @@ def test_two_base_table_can_be_skipped():
     assert d.info["table2_bytes"] == 0 and len(d.tables()["delta2"]) == 0
 
 
+def walk_triples(t, text: bytes):
+    """Three bases per lookup over delta3, as the kernel walks: states past
+    the three-base rows take a delta2 and a delta lookup (or three delta
+    lookups); keywords ending at the first or second base of a step are found
+    through bits 29 / 30 and one or two delta lookups; the text is padded
+    with A to whole steps and ends past it are dropped."""
+    d1, d2, d3 = t["delta"], t["delta2"], t["delta3"]
+    off, pid, plen = t["out_off"], t["out_pid"], t["pat_len"]
+    rows2, rows3 = len(d2) // 16, len(d3) // 64
+    M = 0x3FFFFFFF
+    n = len(text)
+    out = set()
+
+    def emit(state, end):
+        if end < n:
+            for k in range(off[state], off[state + 1]):
+                p = int(pid[k])
+                out.add((end + 1 - int(plen[p]), p))
+
+    codes = [CODE[c] for c in text] + [0, 0]
+    s = 0
+    for i in range(0, n, 3):
+        x, y, z = codes[i], codes[i + 1], codes[i + 2]
+        if s < rows3:
+            e = int(d3[64 * s + (x | (y << 2) | (z << 4))])
+        elif s < rows2:
+            e2 = int(d2[16 * s + (x | (y << 2))])
+            e1 = int(d1[4 * (e2 & M) + z])
+            e = (e1 & 0x9FFFFFFF) | ((e2 >> 1) & 0x60000000)
+        else:
+            a1 = int(d1[4 * s + x])
+            a2 = int(d1[4 * (a1 & M) + y])
+            a3 = int(d1[4 * (a2 & M) + z])
+            e = (a3 & 0x9FFFFFFF) | ((a2 >> 31) << 30) | ((a1 >> 31) << 29)
+        first = int(d1[4 * s + x]) & M
+        if e & (1 << 29):
+            emit(first, i)
+        if e & (1 << 30):
+            emit(int(d1[4 * first + y]) & M, i + 1)
+        s = e & 0x1FFFFFFF
+        if e >> 31:
+            emit(s, i + 2)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("rows3", [None, 1, 7, 0])
+@pytest.mark.parametrize("rows2", [0, 3])
+def test_three_base_table_walk_equals_oracle(seed, rows3, rows2):
+    rng = random.Random(750 + seed)
+    pats = rand_set(rng, rng.randint(1, 50), 1, 9) + ([b"A", b"AA"] if seed % 2 else [])
+    n = rng.choice([0, 1, 2, 3, 4, 5, 52, 701, 2000])
+    text = bytes(rng.choice(b"ACGT") for _ in range(n)) if seed % 3 else (b"ACG" * n)[:n]
+    d = acg.build(pats, host_only=True, stride2_states=rows2, stride3=rows3 is not None, stride3_states=rows3 or 0)
+    t = d.tables()
+    S = len(t["depth"])
+    want3 = 0 if rows3 is None else (S if rows3 == 0 else min(rows3, S))
+    assert len(t["delta3"]) == 64 * want3 and d.info["table3_bytes"] == 256 * want3
+    pos, pid, _ = oracle.Machine(pats).scan(text)
+    assert walk_triples(t, text) == set(zip(pos.tolist(), pid.tolist()))
+
+
+def test_three_base_entries_compose_three_single_steps():
+    rng = random.Random(77)
+    t = acg.build(rand_set(rng, 30, 2, 8), host_only=True).tables()
+    d1, d3 = t["delta"].astype(np.int64), t["delta3"].astype(np.int64)
+    off = t["out_off"]
+    has = lambda u: off[u + 1] > off[u]
+    M = 0x3FFFFFFF
+    for s in range(len(d3) // 64):
+        for sym in range(64):
+            x, y, z = sym & 3, (sym >> 2) & 3, sym >> 4
+            a = int(d1[4 * s + x]) & M
+            b = int(d1[4 * a + y]) & M
+            c = int(d1[4 * b + z]) & M
+            e = int(d3[64 * s + sym])
+            assert e & 0x1FFFFFFF == c
+            assert (e >> 31, (e >> 30) & 1, (e >> 29) & 1) == (int(has(c)), int(has(b)), int(has(a)))
+
+
 def walk_failureless(t, text: bytes):
     """From every start, follow trie edges only and report own keywords."""
     g, off, pid = t["gotos"], t["own_off"], t["own_pid"]

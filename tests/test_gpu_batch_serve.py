@@ -54,7 +54,7 @@ def packed_dev(texts):
 
 
 @pytest.mark.parametrize("form", ["packed_dev", "ascii_dev", "ascii_host", "packed_host"])
-@pytest.mark.parametrize("interleave,stride", [(1, 1), (4, 1), (1, 2), (2, 2)])
+@pytest.mark.parametrize("interleave,stride", [(1, 1), (4, 1), (1, 2), (2, 2), (1, 3), (2, 3)])
 def test_batch_vs_oracle(form, interleave, stride):
     texts, pats = batch_case(11)
     d = acg.build(pats)
@@ -90,7 +90,7 @@ def test_batch_equals_per_text_loop():
     assert np.array_equal(b, loop)
 
 
-@pytest.mark.parametrize("chunk,stride", [(0, 1), (64, 1), (1000, 1), (0, 2), (64, 2)])
+@pytest.mark.parametrize("chunk,stride", [(0, 1), (64, 1), (1000, 1), (0, 2), (64, 2), (0, 3), (1000, 3)])
 def test_batch_plan_replays_exactly(chunk, stride):
     texts, pats = batch_case(13, 100)
     d = acg.build(pats)

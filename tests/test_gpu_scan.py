@@ -78,7 +78,8 @@ def _cases(seed, k):
 
 
 SHAPES = ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8",
-          "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1", "s2rows3", "s2rows40i2"]
+          "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1", "s2rows3", "s2rows40i2",
+          "s3", "s3i2", "s3hot0", "s3hot1", "s3c1", "s3c97", "s3rows3", "s3rows40i2"]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -95,18 +96,22 @@ def test_fuzz_vs_oracle(shape):
             kw["hot_states"] = 1
         elif shape.startswith("i"):
             kw["interleave"] = int(shape[1:])
-        elif shape.startswith("s"):  # two bases per lookup (s1: one, forced)
+        elif shape.startswith("s"):  # two or three bases per lookup (s1: one, forced)
             kw["stride"] = int(shape[1])
             rest = shape[2:]
-            if rest.startswith("rows"):  # two-base rows only for the shallowest states
+            if rest.startswith("rows"):  # multi-base rows only for the shallowest states
                 r_, _, il = rest[4:].partition("i")
-                build_kw["stride2_states"] = int(r_)
+                if kw["stride"] == 3:  # R three-base rows, 2R two-base rows, one-base lookups beyond
+                    build_kw["stride3_states"] = int(r_)
+                    build_kw["stride2_states"] = 2 * int(r_)
+                else:
+                    build_kw["stride2_states"] = int(r_)
                 if il:
                     kw["interleave"] = int(il)
             elif rest.startswith("i"):
                 kw["interleave"] = int(rest[1:])
-            elif rest == "hot0":
-                kw["hot_states"] = 0
+            elif rest.startswith("hot"):
+                kw["hot_states"] = int(rest[3:])
             elif rest.startswith("c"):
                 kw["chunk"] = int(rest[1:])
         d = acg.build(pats, **build_kw)

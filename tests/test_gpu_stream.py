@@ -34,7 +34,7 @@ def _pieces(rng, n, lmax):
 
 
 @pytest.mark.parametrize("form", ["ascii_dev", "ascii_host", "packed_dev", "packed_host"])
-@pytest.mark.parametrize("stride", [1, 2])
+@pytest.mark.parametrize("stride", [1, 2, 3])
 def test_stream_equals_one_scan(form, stride):
     text, pats, rng = _text_and_patterns(31, 60_000)
     d = acg.build(pats)

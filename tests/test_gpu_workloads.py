@@ -2,11 +2,12 @@
 configuration the benchmark times (the library's default shape).
 
   * 256 Mbase Markov chromosome, 10,000 keywords: every occurrence against
-    the oracle's full scan;
+    the oracle's full scan, at one, two and three bases per lookup;
   * 3 Gbase Markov genome, 100,000 keywords: occurrences in 24 sampled
     windows against the oracle run on each window (with the L_max-1 halo),
     plus properties that hold at any size (counts = histogram of the list,
-    sum of counts = occurrences, the same set under a second launch shape);
+    sum of counts = occurrences, the same set under launch shapes reading
+    two and three bases per lookup);
   * 4,096 lognormal texts, 50,000 keywords: the graph-replayed batch and the
     per-text loop against the oracle on every text;
   * the 8 serving sets: requests alone and mixed against the oracle.
@@ -36,7 +37,7 @@ def test_chromosome_full_parity():
     packed = acg.pack(w.text.ascii)
     n = w.text.ascii.numel()
     want, counts = oracle_canonical(w.patterns, w.text.ascii)
-    for stride in (1, 2):
+    for stride in (1, 2, 3):
         r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, stride=stride)
         got = r.canonical()
         assert got.shape == want.shape and np.array_equal(got, want)
@@ -66,6 +67,12 @@ def test_genome_sampled_parity_and_invariants():
     b = torch.sort(_keys(r2.pos, r2.pattern_id))[0]
     assert torch.equal(a, b)
     del r2, b
+    # and three bases per lookup
+    r3 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, stride=3)
+    assert r3.n_matches == k
+    assert torch.equal(a, torch.sort(_keys(r3.pos, r3.pattern_id))[0])
+    assert torch.equal(r.counts, r3.counts)
+    del r3
     assert torch.equal(r.counts, acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=0,
                                           interleave=2, stride=1).counts)
     # sampled windows against the oracle
