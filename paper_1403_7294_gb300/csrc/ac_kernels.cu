@@ -113,6 +113,25 @@ struct Emit {
     uint32_t pid_offset;  // added to every reported keyword id (partitioned keyword sets)
 };
 
+// Fills a block's Emit record field by field (one thread; the caller's
+// barrier publishes it).
+__device__ __forceinline__ void set_emit(Emit& em, const uint32_t* delta, const uint32_t* delta2, uint32_t s2_rows,
+                                         const uint32_t* out_off, const uint2* out_ent, ac_match* matches,
+                                         uint64_t capacity, unsigned long long* counter, unsigned long long* hits,
+                                         uint64_t pos_offset, uint32_t pid_offset) {
+    em.delta = delta;
+    em.delta2 = delta2;
+    em.s2_rows = s2_rows;
+    em.out_off = out_off;
+    em.out_ent = out_ent;
+    em.matches = matches;
+    em.capacity = capacity;
+    em.counter = counter;
+    em.hits = hits;
+    em.pos_offset = pos_offset;
+    em.pid_offset = pid_offset;
+}
+
 // Hits wait in a per-warp queue in shared memory, 16 B per event:
 // {end position bits 0-31, end position bits 32-55 | tag << 24, state, text
 // id}. The tag gives the bases still to be read after `state` to reach the
@@ -495,8 +514,8 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs
     extern __shared__ uint4 sm_rows[];
     __shared__ Emit em;
     if (threadIdx.x == 0)
-        em = Emit{a.delta,    a.delta2,   a.s2_rows, a.out_off, a.out_ent, a.matches,
-                  a.capacity, a.counter,  a.hits,    a.pos_offset, 0u};
+        set_emit(em, a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent, a.matches, a.capacity, a.counter, a.hits,
+                 a.pos_offset, 0u);
     constexpr uint32_t R16 = ST == 1 ? 1 : (ST == 2 ? 4 : 16);  // 16-byte units per row
     stage_hot(sm_rows, ST == 1 ? a.delta : (ST == 2 ? a.delta2 : a.delta3), hot * R16);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
@@ -533,7 +552,8 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) batch_kernel(BatchAr
     extern __shared__ uint4 sm_rows[];
     __shared__ Emit em;
     if (threadIdx.x == 0)
-        em = Emit{a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent, a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+        set_emit(em, a.delta, a.delta2, a.s2_rows, a.out_off, a.out_ent, a.matches, a.capacity, a.counter, a.hits,
+                 0ull, 0u);
     constexpr uint32_t R16 = ST == 1 ? 1 : (ST == 2 ? 4 : 16);
     stage_hot(sm_rows, ST == 1 ? a.delta : (ST == 2 ? a.delta2 : a.delta3), hot * R16);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
@@ -581,8 +601,8 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
     __shared__ Emit em;
     const PartDesc pd = a.parts[blockIdx.y];
     if (threadIdx.x == 0)
-        em = Emit{pd.delta, nullptr, 0u, pd.out_off, pd.out_ent, a.matches, a.capacity, a.counter, pd.hits, 0ull,
-                  pd.pid_offset};
+        set_emit(em, pd.delta, nullptr, 0u, pd.out_off, pd.out_ent, a.matches, a.capacity, a.counter, pd.hits, 0ull,
+                 pd.pid_offset);
     stage_hot(sm_rows, pd.delta, pd.n_states);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
@@ -620,7 +640,7 @@ __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t ho
     extern __shared__ uint4 sm_rows[];
     __shared__ Emit em;  // no multi-base steps here: the drain needs no transition table
     if (threadIdx.x == 0)
-        em = Emit{nullptr, nullptr, 0u, a.own_off, a.own_ent, a.matches, a.capacity, a.counter, a.hits, 0ull, 0u};
+        set_emit(em, nullptr, nullptr, 0u, a.own_off, a.own_ent, a.matches, a.capacity, a.counter, a.hits, 0ull, 0u);
     stage_hot(sm_rows, a.gotos, hot);  // its barrier also publishes em
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
