@@ -109,8 +109,25 @@ bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out) {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_locked();
     if (g_cache.empty()) return false;
-    auto it = g_cache.find(Key{device_tag(), size_class(dfa->host.n_states), size_class(n)});
-    if (it == g_cache.end()) return false;
+    const std::string dev = device_tag();
+    const unsigned sc = size_class(dfa->host.n_states), nc = size_class(n);
+    auto it = g_cache.find(Key{dev, sc, nc});
+    if (it == g_cache.end()) {
+        // no shape tuned for this text size: take the one tuned for the nearest
+        // text size on the same device and machine size (the table's placement
+        // is what the shape mostly reflects; chunks are recomputed for n)
+        unsigned best_d = ~0u;
+        for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt) {
+            if (std::get<0>(jt->first) != dev || std::get<1>(jt->first) != sc) continue;
+            const unsigned c = std::get<2>(jt->first);
+            const unsigned d = c > nc ? c - nc : nc - c;
+            if (d < best_d || (d == best_d && c > std::get<2>(it->first))) {
+                best_d = d;
+                it = jt;
+            }
+        }
+        if (it == g_cache.end()) return false;
+    }
     out->threads = it->second.threads;
     out->interleave = it->second.interleave;
     out->hot = it->second.hot;

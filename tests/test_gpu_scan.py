@@ -211,6 +211,23 @@ def test_plain_1mbase_uniform_full():
     assert r.stats["scan_ms"] > 0
 
 
+def test_tuned_shape_serves_nearby_text_sizes():
+    """A shape tuned for one text size is used for a text of another size
+    (same machine size, nearest tuned text size), and stays exact."""
+    rng = random.Random(10)
+    text = rand_dna(rng, 3 << 20)
+    pats = [text[j : j + rng.randint(9, 15)] for j in rng.sample(range((3 << 20) - 20), 3000)]
+    d = acg.build(pats)
+    packed = acg.pack(to_dev(text))
+    best = acg.autotune(d, packed, len(text))
+    part = text[: 600_000]
+    want, counts = oracle_canonical(pats, part)
+    r = acg.scan(d, to_dev(part), stats=True)
+    assert_same(r, want, counts)
+    assert (r.stats["stride"], r.stats["threads"], r.stats["interleave"]) == (
+        best["stride"], best["threads"], best["interleave"])
+
+
 def test_autotune_then_exact():
     rng = random.Random(9)
     text = rand_dna(rng, 1 << 20)
@@ -218,7 +235,8 @@ def test_autotune_then_exact():
     d = acg.build(pats)
     packed = acg.pack(to_dev(text))
     best = acg.autotune(d, packed, len(text))
-    assert best["interleave"] in (1, 2, 4, 8) and best["threads"] in (256, 512, 1024)
+    assert best["interleave"] in (1, 2, 4, 8) and best["threads"] in (256, 512, 768, 1024)
+    assert best["stride"] in (1, 2, 3)
     want, counts = oracle_canonical(pats, text)
     r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), threads=best["threads"],
                  interleave=best["interleave"], hot_states=best["hot_states"])
