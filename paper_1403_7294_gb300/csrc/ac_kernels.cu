@@ -307,10 +307,10 @@ __device__ __forceinline__ void idle_chain(Chain& c, const uint32_t* text, uint6
 }
 
 // Threads per block each (interleave, stride) pair is compiled for (register
-// budget: the three-base walk holds 192 bases of text per chain).
+// budget).
 template <int I, int ST = 1>
 struct MaxThreads {
-    static constexpr int value = I == 1 ? (ST == 3 ? 768 : 1024) : (I <= 4 ? 512 : 256);
+    static constexpr int value = I == 1 ? 1024 : (I <= 4 ? 512 : 256);
 };
 
 // Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
@@ -400,104 +400,117 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
     if (qn) drain(q, qn, em);
 }
 
-// Walk I chains in lockstep three bases per lookup: the three-base row for
-// states [0, s3_rows) (from shared memory below `hot`), a two-base and a
-// one-base lookup for the states with a two-base row, three one-base lookups
-// beyond. A step's entry has one flag per base entered (bits 29, 30, 31: a
-// keyword ends after the first, second, third base). The text is loaded 192
-// bases (three 16-byte loads) at a time and consumed 48 bases (three words,
-// sixteen steps) at a time.
+// Walk I chains three bases per lookup where the tables allow it, every lane
+// on its own schedule: each iteration makes exactly one lookup per chain -
+// three bases from a three-base row (states [0, s3_rows), from shared memory
+// below `hot`), two from a two-base row ([s3_rows, s2_rows)) or one from the
+// base table - so a lane in a deep state never holds the others up (steps in
+// lockstep would wait for the warp's longest chain of dependent lookups).
+// A lookup's entry has one flag per base entered (three-base rows: bits 29,
+// 30, 31 after the first, second, third base; two-base rows: bits 30, 31).
+// Each lane reads its text through a 64-base block, the next block already
+// loading, into a bit buffer of the coming bases.
 template <int I>
 __device__ __forceinline__ void walk3(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                       const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
-    constexpr uint32_t FLAGS = AC_FLAG | AC_FLAG_MID | AC_FLAG_MID1;
-    uint32_t nb = 0;
+    const uint32_t lt = lanemask_lt();
+    uint32_t s[I], pos[I], nb[I], wi[I];
+    uint64_t bits[I], nextw[I];
+    uint4 cur[I], nxt[I];
 #pragma unroll
     for (int j = 0; j < I; ++j) {
-        const uint32_t b = (ch[j].hi + 191) / 192;
-        nb = b > nb ? b : nb;
+        s[j] = 0;
+        pos[j] = 0;  // next base to read, relative to ch[j].start
+        nb[j] = 0;   // bases in bits[j]
+        wi[j] = 0;   // next word of cur[j]
+        bits[j] = 0;
+        const uint64_t w0 = ch[j].start >> 4;
+        const bool live = ch[j].hi > 0;
+        cur[j] = live ? load_block(ch[j].text, w0, ch[j].nwords, pol_txt) : make_uint4(0, 0, 0, 0);
+        nxt[j] = live ? load_block(ch[j].text, w0 + 4, ch[j].nwords, pol_txt) : make_uint4(0, 0, 0, 0);
+        nextw[j] = w0 + 8;
     }
-    nb = __reduce_max_sync(FULL, nb);
-    const uint32_t lt = lanemask_lt();
-    uint32_t s[I];
-#pragma unroll
-    for (int j = 0; j < I; ++j) s[j] = 0;
     uint32_t qn = 0;  // queued events (same value in every lane)
-
-    for (uint32_t b = 0; b < nb; ++b) {
-        uint32_t w[I][12];
-        uint32_t fmask[I];
+    for (;;) {
+        bool act[I];
+        bool any_act = false;
 #pragma unroll
         for (int j = 0; j < I; ++j) {
-            const bool act = 192u * b < ch[j].hi;
-            fmask[j] = act ? FLAGS : 0u;
-            const uint64_t w0 = (ch[j].start >> 4) + 12ull * b;
+            act[j] = pos[j] < ch[j].hi;
+            any_act |= act[j];
+        }
+        if (!__any_sync(FULL, any_act)) break;
+        uint32_t e[I], k[I], sym[I];
 #pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                const uint4 x = act ? load_block(ch[j].text, w0 + 4 * v, ch[j].nwords, pol_txt) : make_uint4(0, 0, 0, 0);
-                w[j][4 * v] = x.x;
-                w[j][4 * v + 1] = x.y;
-                w[j][4 * v + 2] = x.z;
-                w[j][4 * v + 3] = x.w;
+        for (int j = 0; j < I; ++j) {
+            if (act[j] && nb[j] < 3) {  // 16 more bases into the buffer
+                if (wi[j] == 4) {
+                    cur[j] = nxt[j];
+                    nxt[j] = load_block(ch[j].text, nextw[j], ch[j].nwords, pol_txt);
+                    nextw[j] += 4;
+                    wi[j] = 0;
+                }
+                const uint32_t w = wi[j] == 0 ? cur[j].x : (wi[j] == 1 ? cur[j].y : (wi[j] == 2 ? cur[j].z : cur[j].w));
+                bits[j] |= (uint64_t)w << (2 * nb[j]);
+                nb[j] += 16;
+                ++wi[j];
+            }
+            const uint32_t cs = s[j];
+            sym[j] = (uint32_t)bits[j] & 63u;
+            const uint32_t* tab;
+            uint32_t idx;
+            if (cs < tb.s3_rows) {
+                k[j] = 3;
+                idx = (cs << 6) | sym[j];
+                tab = tb.delta3;
+            } else if (cs < tb.s2_rows) {
+                k[j] = 2;
+                idx = (cs << 4) | (sym[j] & 15u);
+                tab = tb.delta2;
+            } else {
+                k[j] = 1;
+                idx = (cs << 2) | (sym[j] & 3u);
+                tab = tb.delta;
+            }
+            e[j] = act[j] ? ((cs < hot) ? sm[idx] : ld_table(tab + idx, pol_tab)) : 0u;
+        }
+        uint32_t any = 0, nx[I];
+        bool fin[I], m1[I], m2[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const bool k3 = k[j] == 3;
+            nx[j] = e[j] & (k3 ? AC_STATE_MASK3 : AC_STATE_MASK);
+            fin[j] = (e[j] & AC_FLAG) != 0;
+            m1[j] = k3 ? (e[j] & AC_FLAG_MID1) != 0 : (k[j] == 2 && (e[j] & AC_FLAG_MID) != 0);
+            m2[j] = k3 && (e[j] & AC_FLAG_MID) != 0;
+            any |= (uint32_t)(fin[j] | m1[j] | m2[j]);
+        }
+        if (__any_sync(FULL, any)) {
+#pragma unroll
+            for (int j = 0; j < I; ++j) {
+                const uint32_t p = pos[j];
+                const bool h1 = m1[j] && p >= ch[j].lo && p < ch[j].hi;
+                const uint32_t b1 = __ballot_sync(FULL, h1);
+                if (b1) append(q, qn, b1, h1, ch[j].start + p, tag1(sym[j] & 3u), s[j], ch[j].text_id, lt, em);
+                const bool h2 = m2[j] && p + 1 >= ch[j].lo && p + 1 < ch[j].hi;
+                const uint32_t b2 = __ballot_sync(FULL, h2);
+                if (b2)
+                    append(q, qn, b2, h2, ch[j].start + p + 1, tag2(sym[j] & 3u, (sym[j] >> 2) & 3u), s[j],
+                           ch[j].text_id, lt, em);
+                const uint32_t pe = p + k[j] - 1;  // last base of this lookup
+                const bool hf = fin[j] && pe >= ch[j].lo && pe < ch[j].hi;
+                const uint32_t bf = __ballot_sync(FULL, hf);
+                if (bf) append(q, qn, bf, hf, ch[j].start + pe, 0u, nx[j], ch[j].text_id, lt, em);
             }
         }
-#pragma unroll 1
-        for (uint32_t g = 0; g < 4; ++g) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int o = 6 * k, wi = o >> 5, sh = o & 31;  // the step's 6 bits within words 0-2
-                uint32_t e[I], sp[I], sy[I];
-#pragma unroll
-                for (int j = 0; j < I; ++j) {
-                    sy[j] = (sh <= 26 ? (w[j][wi] >> sh) : __funnelshift_r(w[j][wi], w[j][wi + 1], sh)) & 63u;
-                    const uint32_t cur = s[j];
-                    if (cur < tb.s3_rows) {
-                        const uint32_t idx = (cur << 6) | sy[j];
-                        e[j] = (cur < hot) ? sm[idx] : ld_table(tb.delta3 + idx, pol_tab);
-                    } else if (cur < tb.s2_rows) {  // two bases, then one
-                        const uint32_t e2 = ld_table(tb.delta2 + ((cur << 4) | (sy[j] & 15u)), pol_tab);
-                        const uint32_t e1 = ld_table(tb.delta + (((e2 & AC_STATE_MASK) << 2) | (sy[j] >> 4)), pol_tab);
-                        e[j] = (e1 & (AC_FLAG | AC_STATE_MASK3)) | ((e2 >> 1) & (AC_FLAG_MID | AC_FLAG_MID1));
-                    } else {  // deep state: three one-base lookups
-                        const uint32_t a1 = ld_table(tb.delta + ((cur << 2) | (sy[j] & 3u)), pol_tab);
-                        const uint32_t a2 =
-                            ld_table(tb.delta + (((a1 & AC_STATE_MASK) << 2) | ((sy[j] >> 2) & 3u)), pol_tab);
-                        const uint32_t a3 = ld_table(tb.delta + (((a2 & AC_STATE_MASK) << 2) | (sy[j] >> 4)), pol_tab);
-                        e[j] = (a3 & (AC_FLAG | AC_STATE_MASK3)) | ((a2 & AC_FLAG) >> 1) | ((a1 & AC_FLAG) >> 2);
-                    }
-                }
-                uint32_t any = 0;
-#pragma unroll
-                for (int j = 0; j < I; ++j) {
-                    sp[j] = s[j];
-                    s[j] = e[j] & AC_STATE_MASK3;
-                    any |= e[j] & fmask[j];
-                }
-                if (__any_sync(FULL, any)) {
-                    const uint32_t off = 192u * b + 48u * g + 3u * k;  // first base of this step
-#pragma unroll
-                    for (int j = 0; j < I; ++j) {
-                        const bool h1 = (e[j] & fmask[j] & AC_FLAG_MID1) && off >= ch[j].lo && off < ch[j].hi;
-                        const uint32_t m1 = __ballot_sync(FULL, h1);
-                        if (m1)
-                            append(q, qn, m1, h1, ch[j].start + off, tag1(sy[j] & 3u), sp[j], ch[j].text_id, lt, em);
-                        const bool h2 =
-                            (e[j] & fmask[j] & AC_FLAG_MID) && off + 1 >= ch[j].lo && off + 1 < ch[j].hi;
-                        const uint32_t m2 = __ballot_sync(FULL, h2);
-                        if (m2)
-                            append(q, qn, m2, h2, ch[j].start + off + 1, tag2(sy[j] & 3u, (sy[j] >> 2) & 3u), sp[j],
-                                   ch[j].text_id, lt, em);
-                        const bool h3 = (e[j] & fmask[j] & AC_FLAG) && off + 2 >= ch[j].lo && off + 2 < ch[j].hi;
-                        const uint32_t m3 = __ballot_sync(FULL, h3);
-                        if (m3) append(q, qn, m3, h3, ch[j].start + off + 2, 0u, s[j], ch[j].text_id, lt, em);
-                    }
-                }
+        for (int j = 0; j < I; ++j)
+            if (act[j]) {
+                s[j] = nx[j];
+                bits[j] >>= 2 * k[j];
+                nb[j] -= k[j];
+                pos[j] += k[j];
             }
-#pragma unroll
-            for (int j = 0; j < I; ++j)  // the next 48 bases move to words 0-2
-#pragma unroll
-                for (int v = 0; v < 9; ++v) w[j][v] = w[j][v + 3];
-        }
     }
     if (qn) drain(q, qn, em);
 }

@@ -234,11 +234,12 @@ def test_two_base_table_can_be_skipped():
 
 
 def walk_triples(t, text: bytes):
-    """Three bases per lookup over delta3, as the kernel walks: states past
-    the three-base rows take a delta2 and a delta lookup (or three delta
-    lookups); keywords ending at the first or second base of a step are found
-    through bits 29 / 30 and one or two delta lookups; the text is padded
-    with A to whole steps and ends past it are dropped."""
+    """The three-base walk as the kernel takes it: from a state with a
+    three-base row read three bases, from one with a two-base row two, else
+    one; a keyword ending at the first or second base of a lookup is found
+    through bit 29 / 30 (three-base rows) or bit 30 (two-base rows) and one or
+    two delta lookups; bases past the text read as A and ends past it are
+    dropped."""
     d1, d2, d3 = t["delta"], t["delta2"], t["delta3"]
     off, pid, plen = t["out_off"], t["out_pid"], t["pat_len"]
     rows2, rows3 = len(d2) // 16, len(d3) // 64
@@ -253,28 +254,28 @@ def walk_triples(t, text: bytes):
                 out.add((end + 1 - int(plen[p]), p))
 
     codes = [CODE[c] for c in text] + [0, 0]
-    s = 0
-    for i in range(0, n, 3):
+    s, i = 0, 0
+    while i < n:
         x, y, z = codes[i], codes[i + 1], codes[i + 2]
+        first = int(d1[4 * s + x]) & M
         if s < rows3:
             e = int(d3[64 * s + (x | (y << 2) | (z << 4))])
+            if e & (1 << 29):
+                emit(first, i)
+            if e & (1 << 30):
+                emit(int(d1[4 * first + y]) & M, i + 1)
+            s, k = e & 0x1FFFFFFF, 3
         elif s < rows2:
-            e2 = int(d2[16 * s + (x | (y << 2))])
-            e1 = int(d1[4 * (e2 & M) + z])
-            e = (e1 & 0x9FFFFFFF) | ((e2 >> 1) & 0x60000000)
+            e = int(d2[16 * s + (x | (y << 2))])
+            if e & (1 << 30):
+                emit(first, i)
+            s, k = e & M, 2
         else:
-            a1 = int(d1[4 * s + x])
-            a2 = int(d1[4 * (a1 & M) + y])
-            a3 = int(d1[4 * (a2 & M) + z])
-            e = (a3 & 0x9FFFFFFF) | ((a2 >> 31) << 30) | ((a1 >> 31) << 29)
-        first = int(d1[4 * s + x]) & M
-        if e & (1 << 29):
-            emit(first, i)
-        if e & (1 << 30):
-            emit(int(d1[4 * first + y]) & M, i + 1)
-        s = e & 0x1FFFFFFF
+            e = int(d1[4 * s + x])
+            s, k = e & M, 1
         if e >> 31:
-            emit(s, i + 2)
+            emit(s, i + k - 1)
+        i += k
     return out
 
 
