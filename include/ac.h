@@ -83,8 +83,8 @@ enum ac_build_flags {
 typedef struct {
     uint32_t flags;          /* ac_build_flags                                           */
     uint32_t stride2_states; /* rows of the two-base table: the first (breadth-first, i.e.
-                                shallowest) this many states; 0 = min(S, 2^19). Steps from
-                                deeper states take two one-base lookups instead.          */
+                                shallowest) this many states; 0 = every state, up to 2^24.
+                                Steps from deeper states take two one-base lookups.       */
     uint32_t stride3_states; /* rows of the three-base table, likewise; 0 = min(S, 2^17);
                                 at most 2^22. Three-base steps from deeper states take a
                                 two-base and a one-base lookup (or three one-base ones).  */

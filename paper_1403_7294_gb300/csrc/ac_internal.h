@@ -15,7 +15,9 @@ static constexpr uint32_t AC_FLAG_MID = 0x40000000u;
 static constexpr uint32_t AC_STATE_MASK = 0x3fffffffu;
 static constexpr uint32_t AC_MAX_STATES = 1u << 27;          // 16 B rows stay below 2 GiB
 static constexpr uint32_t AC_MAX_STATES_STRIDE2 = 1u << 24;  // 64 B rows stay below 1 GiB
-static constexpr uint32_t AC_DEFAULT_STRIDE2_ROWS = 1u << 19;  // 32 MiB of two-base rows
+// Two-base rows for every state by default: a lockstep warp then never waits
+// for a lane's second dependent lookup (64 B per state).
+static constexpr uint32_t AC_DEFAULT_STRIDE2_ROWS = 1u << 24;
 // Three-base table: bit 29 "the state after the first base has output", bit
 // 30 "after the second", bit 31 "after the third"; the state in bits 0-28.
 static constexpr uint32_t AC_FLAG_MID1 = 0x20000000u;
