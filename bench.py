@@ -85,6 +85,34 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+# DRAM traffic of the scan kernel per base of the genome workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch over a
+# 1 Gbase slice of the same generator, the shape tuned for it); a 3 Gbase launch
+# is scaled by its bases (traffic grows with the text). It holds only for the
+# library sources it was taken from: the hash below; otherwise traffic is null.
+TRAFFIC_CAPTURE = {"workload": "genome", "sources_sha256": "45b57026bee81e28b6517d251f34d967a59fc5004d133bfdf5af98eb37504442",
+                   "bytes_per_base": (2.077779e9 + 2.594400e9) / 1e9,
+                   "capture": "profiles/scan_kernel_genome_1gbase_full.md"}
+TRAFFIC_SOURCES = ("ac_kernels.cu", "ac_internal.h", "ac_builder.cpp", "ac_api.cu", "ac_tune.cpp")
+
+
+def library_sources_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1403_7294_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, n_bases: int):
+    c = TRAFFIC_CAPTURE
+    if c["bytes_per_base"] is None or workload != c["workload"] or library_sources_sha() != c["sources_sha256"]:
+        return None
+    return int(round(c["bytes_per_base"] * n_bases))
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -264,7 +292,7 @@ def run_plain(args, world, rank, local):
     achieved = alg_bytes / (scan_avg / 1e3) / 1e9
     out["roofline"] = {
         "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-        "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_kind,
+        "frac": round(achieved / peak, 5), "traffic": measured_traffic(args.workload, n), "peak_source": peak_kind,
         "kernel": "scan_kernel", "kernel_ms": round(scan_avg, 4),
         "algorithmic_bytes": int(alg_bytes),
         "walked_bases_per_s": round(stats.bases_walked / (scan_avg / 1e3), 1),  # owned bases plus halo re-reads
