@@ -24,6 +24,9 @@
 #include <cstring>
 #include <deque>
 #include <new>
+#include <system_error>
+#include <thread>
+#include <vector>
 
 #include "ac_internal.h"
 
@@ -41,6 +44,29 @@ inline int base_code(uint8_t c, bool fold) {
         case 't': return fold ? 3 : -1;
         default: return -1;
     }
+}
+
+// Runs f(s) for s in [0, rows) on the host's cores (rows are independent).
+template <typename F>
+void parallel_rows(uint32_t rows, F&& f) {
+    const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const uint32_t T = rows < 4096 ? 1u : hw;
+    if (T == 1) {
+        for (uint32_t s = 0; s < rows; ++s) f(s);
+        return;
+    }
+    auto range = [&](uint32_t t) {
+        const uint32_t a = (uint32_t)((uint64_t)rows * t / T), b = (uint32_t)((uint64_t)rows * (t + 1) / T);
+        for (uint32_t s = a; s < b; ++s) f(s);
+    };
+    std::vector<std::thread> pool;
+    uint32_t spawned = 0;
+    try {
+        for (; spawned < T; ++spawned) pool.emplace_back(range, spawned);
+    } catch (const std::system_error&) {  // no more threads: the rest on this one
+    }
+    for (uint32_t t = spawned; t < T; ++t) range(t);
+    for (auto& th : pool) th.join();
 }
 
 }  // namespace
@@ -222,7 +248,7 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
             t->s2_rows = std::min<uint32_t>(rows, AC_MAX_STATES_STRIDE2);
             t->delta2.assign((size_t)t->s2_rows * 16, 0);
             auto has_out = [&](uint32_t u) { return t->out_off[u + 1] > t->out_off[u]; };
-            for (uint32_t s = 0; s < t->s2_rows; ++s)
+            parallel_rows(t->s2_rows, [&](uint32_t s) {
                 for (uint32_t x = 0; x < 4; ++x) {
                     const uint32_t m = t->delta[(size_t)s * 4 + x] & AC_STATE_MASK;
                     for (uint32_t y = 0; y < 4; ++y) {
@@ -231,6 +257,7 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
                             f | (has_out(f) ? AC_FLAG : 0u) | (has_out(m) ? AC_FLAG_MID : 0u);
                     }
                 }
+            });
         }
 
         // ---- three bases per lookup: delta3[s][x | y << 2 | z << 4], bits 0-28 the
@@ -242,7 +269,7 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
             t->s3_rows = std::min<uint32_t>(rows, AC_MAX_STATES_STRIDE3);
             t->delta3.assign((size_t)t->s3_rows * 64, 0);
             auto has_out = [&](uint32_t u) { return t->out_off[u + 1] > t->out_off[u]; };
-            for (uint32_t s = 0; s < t->s3_rows; ++s)
+            parallel_rows(t->s3_rows, [&](uint32_t s) {
                 for (uint32_t x = 0; x < 4; ++x) {
                     const uint32_t a = t->delta[(size_t)s * 4 + x] & AC_STATE_MASK;
                     for (uint32_t y = 0; y < 4; ++y) {
@@ -255,6 +282,7 @@ int ac_build_host(const char* const* patterns, const uint32_t* lens, uint32_t n,
                         }
                     }
                 }
+            });
         }
     } catch (const std::bad_alloc&) {
         return AC_ERR_OOM;

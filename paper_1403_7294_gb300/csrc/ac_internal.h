@@ -22,7 +22,9 @@ static constexpr uint32_t AC_DEFAULT_STRIDE2_ROWS = 1u << 24;
 // 30 "after the second", bit 31 "after the third"; the state in bits 0-28.
 static constexpr uint32_t AC_FLAG_MID1 = 0x20000000u;
 static constexpr uint32_t AC_STATE_MASK3 = 0x1fffffffu;
-static constexpr uint32_t AC_DEFAULT_STRIDE3_ROWS = 1u << 17;  // 32 MiB of three-base rows
+// Three-base rows for every state of machines up to 2M states (512 MiB at most):
+// with all states covered the three-base walk runs its lanes in lockstep.
+static constexpr uint32_t AC_DEFAULT_STRIDE3_ROWS = 1u << 21;
 static constexpr uint32_t AC_MAX_STATES_STRIDE3 = 1u << 22;    // 256 B rows stay at 1 GiB
 // Texts are shorter than 2^56 bases: a queued hit keeps its end position in
 // 56 bits and a tag in the top byte.

@@ -78,6 +78,13 @@ __device__ __forceinline__ uint4 ld_text4(const uint32_t* p, uint64_t pol) {
     return v;
 }
 
+// One text word through L1 (a lane's following words hit the same line), L2 evict-first.
+__device__ __forceinline__ uint32_t ld_text1(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // 64 bases starting at word w (w % 4 == 0); words past the end read as 0.
 __device__ __forceinline__ uint4 load_block(const uint32_t* text, uint64_t w, uint64_t nwords, uint64_t pol) {
     if (w + 4 <= nwords) return ld_text4(text + w, pol);
@@ -94,7 +101,8 @@ struct Tables {
     const uint32_t* __restrict__ delta2;
     uint32_t s2_rows;  // states [0, s2_rows) have two-base rows
     const uint32_t* __restrict__ delta3;
-    uint32_t s3_rows;  // states [0, s3_rows) have three-base rows
+    uint32_t s3_rows;   // states [0, s3_rows) have three-base rows
+    uint32_t n_states;  // all states have three-base rows when s3_rows == n_states
 };
 
 // What drain() reads: one copy per block in shared memory, so the walk keeps
@@ -309,7 +317,7 @@ __device__ __forceinline__ void idle_chain(Chain& c, const uint32_t* text, uint6
 // Threads per block each (interleave, stride) pair is compiled for (register
 // budget).
 template <int I, int ST = 1>
-struct MaxThreads {
+struct MaxThreads {  // ST 1-4 as in walk_any
     static constexpr int value = I == 1 ? 1024 : (I <= 4 ? 512 : 256);
 };
 
@@ -411,8 +419,9 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
 // Each lane reads its text through a 64-base block, the next block already
 // loading, into a bit buffer of the coming bases.
 template <int I>
-__device__ __forceinline__ void walk3(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
-                                      const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
+__device__ __forceinline__ void walk3_free(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
+                                           const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
+                                           uint64_t pol_txt) {
     const uint32_t lt = lanemask_lt();
     uint32_t s[I], pos[I], nb[I], wi[I];
     uint64_t bits[I], nextw[I];
@@ -515,6 +524,95 @@ __device__ __forceinline__ void walk3(const Chain (&ch)[I], const uint32_t* __re
     if (qn) drain(q, qn, em);
 }
 
+// Walk I chains in lockstep three bases per lookup, for machines whose
+// three-base table covers every state: each step is one lookup for every
+// lane, so no lane waits on another, and the hits of a step are voted on
+// together. The text is read 48 bases (three words, sixteen steps) at a time
+// through L1: a lane's next groups come from the same cached line.
+template <int I>
+__device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
+                                           const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
+                                           uint64_t pol_txt) {
+    constexpr uint32_t FLAGS = AC_FLAG | AC_FLAG_MID | AC_FLAG_MID1;
+    uint32_t ng = 0;  // 48-base groups
+#pragma unroll
+    for (int j = 0; j < I; ++j) {
+        const uint32_t g = (ch[j].hi + 47) / 48;
+        ng = g > ng ? g : ng;
+    }
+    ng = __reduce_max_sync(FULL, ng);
+    const uint32_t lt = lanemask_lt();
+    uint32_t s[I];
+#pragma unroll
+    for (int j = 0; j < I; ++j) s[j] = 0;
+    uint32_t qn = 0;  // queued events (same value in every lane)
+    for (uint32_t g = 0; g < ng; ++g) {
+        uint32_t w[I][3];
+        uint32_t fmask[I];
+#pragma unroll
+        for (int j = 0; j < I; ++j) {
+            const bool act = 48u * g < ch[j].hi;
+            fmask[j] = act ? FLAGS : 0u;
+            const uint64_t w0 = (ch[j].start >> 4) + 3ull * g;
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                w[j][v] = (act && w0 + v < ch[j].nwords) ? ld_text1(ch[j].text + w0 + v, pol_txt) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int o = 6 * k, wi = o >> 5, sh = o & 31;  // the step's 6 bits within the 3 words
+            uint32_t e[I], sp[I], sy[I];
+#pragma unroll
+            for (int j = 0; j < I; ++j) {
+                sy[j] = (sh <= 26 ? (w[j][wi] >> sh) : __funnelshift_r(w[j][wi], w[j][wi + 1], sh)) & 63u;
+                const uint32_t idx = (s[j] << 6) | sy[j];
+                e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta3 + idx, pol_tab);
+            }
+            uint32_t any = 0;
+#pragma unroll
+            for (int j = 0; j < I; ++j) {
+                sp[j] = s[j];
+                s[j] = e[j] & AC_STATE_MASK3;
+                any |= e[j] & fmask[j];
+            }
+            if (__any_sync(FULL, any)) {
+                const uint32_t off = 48u * g + 3u * k;  // first base of this step
+#pragma unroll
+                for (int j = 0; j < I; ++j) {
+                    const bool h1 = (e[j] & fmask[j] & AC_FLAG_MID1) && off >= ch[j].lo && off < ch[j].hi;
+                    const uint32_t m1 = __ballot_sync(FULL, h1);
+                    if (m1) append(q, qn, m1, h1, ch[j].start + off, tag1(sy[j] & 3u), sp[j], ch[j].text_id, lt, em);
+                    const bool h2 = (e[j] & fmask[j] & AC_FLAG_MID) && off + 1 >= ch[j].lo && off + 1 < ch[j].hi;
+                    const uint32_t m2 = __ballot_sync(FULL, h2);
+                    if (m2)
+                        append(q, qn, m2, h2, ch[j].start + off + 1, tag2(sy[j] & 3u, (sy[j] >> 2) & 3u), sp[j],
+                               ch[j].text_id, lt, em);
+                    const bool h3 = (e[j] & fmask[j] & AC_FLAG) && off + 2 >= ch[j].lo && off + 2 < ch[j].hi;
+                    const uint32_t m3 = __ballot_sync(FULL, h3);
+                    if (m3) append(q, qn, m3, h3, ch[j].start + off + 2, 0u, s[j], ch[j].text_id, lt, em);
+                }
+            }
+        }
+    }
+    if (qn) drain(q, qn, em);
+}
+
+// Kernel variants by ST: 1 and 2 the lockstep walk at one or two bases per
+// lookup; 3 the three-base walk with lanes on their own schedules; 4 the
+// lockstep three-base walk, used when every state has a three-base row (the
+// launchers pick 3 or 4 for a requested stride of 3).
+template <int I, int ST>
+__device__ __forceinline__ void walk_any(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
+                                         const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
+                                         uint64_t pol_txt) {
+    if constexpr (ST == 4)
+        walk3_lock<I>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+    else if constexpr (ST == 3)
+        walk3_free<I>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+    else
+        walk<I, ST>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+}
+
 // Copies `rows16` 16-byte rows (the hot prefix of the table) to shared memory.
 __device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* table, uint32_t rows16) {
     const uint4* g = reinterpret_cast<const uint4*>(table);
@@ -534,7 +632,7 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows, a.n_states};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -551,10 +649,7 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs
                 idle_chain(ch[j], a.text, nwords, a.text_id);
             }
         }
-        if constexpr (ST == 3)
-            walk3<I>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
-        else
-            walk<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        walk_any<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -572,7 +667,7 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) batch_kernel(BatchAr
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows};
+    const Tables tb{a.delta, a.delta2, a.s2_rows, a.delta3, a.s3_rows, a.n_states};
     uint4* q = sm_rows + hot * R16 + (threadIdx.x >> 5) * QCAP;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -596,10 +691,7 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) batch_kernel(BatchAr
                 set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
             }
         }
-        if constexpr (ST == 3)
-            walk3<I>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
-        else
-            walk<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        walk_any<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -620,7 +712,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
     const uint32_t* sm = reinterpret_cast<const uint32_t*>(sm_rows);
     const uint64_t pol_tab = policy_evict_last();
     const uint64_t pol_txt = policy_evict_first();
-    const Tables tb{pd.delta, nullptr, 0u, nullptr, 0u};
+    const Tables tb{pd.delta, nullptr, 0u, nullptr, 0u, pd.n_states};
     uint4* q = sm_rows + a.max_states + (threadIdx.x >> 5) * QCAP;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,6 +892,11 @@ int dispatch(uint32_t interleave, uint32_t stride, F&& f) {
             case 1: return f.template operator()<1, 3>();
             case 2: return f.template operator()<2, 3>();
         }
+    } else if (stride == 4) {  // three bases in lockstep (every state has a three-base row)
+        switch (interleave) {
+            case 1: return f.template operator()<1, 4>();
+            case 2: return f.template operator()<2, 4>();
+        }
     }
     return -1;
 }
@@ -849,7 +946,7 @@ bool ac_shape_compiled(uint32_t interleave, uint32_t stride) {
 constexpr size_t kStaticSmem = 256;
 static_assert(sizeof(Emit) <= kStaticSmem, "Emit fits the reserve");
 
-static size_t row_bytes(uint32_t stride) { return stride == 3 ? 256 : (stride == 2 ? 64 : 16); }
+static size_t row_bytes(uint32_t stride) { return stride >= 3 ? 256 : (stride == 2 ? 64 : 16); }
 
 size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads, uint32_t stride) {
     return (size_t)hot * row_bytes(stride) + (size_t)(threads / 32) * QCAP * 16;
@@ -945,20 +1042,23 @@ int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream) {
     if (owned == 0) return 0;
     if ((sh.stride == 2 && !a.delta2) || (sh.stride == 3 && !a.delta3)) return (int)cudaErrorInvalidValue;
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
-    const int rc = dispatch(sh.interleave, sh.stride, ScanLaunch{a, sh, n_chunks, (cudaStream_t)stream});
+    const uint32_t code = (sh.stride == 3 && a.s3_rows >= a.n_states) ? 4u : sh.stride;
+    const int rc = dispatch(sh.interleave, code, ScanLaunch{a, sh, n_chunks, (cudaStream_t)stream});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
 int ac_launch_batch(const BatchArgs& a, const ScanShape& sh, void* stream) {
     if (a.n_items == 0) return 0;
     if ((sh.stride == 2 && !a.delta2) || (sh.stride == 3 && !a.delta3)) return (int)cudaErrorInvalidValue;
-    const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{a, sh, (cudaStream_t)stream, false});
+    const uint32_t code = (sh.stride == 3 && a.s3_rows >= a.n_states) ? 4u : sh.stride;
+    const int rc = dispatch(sh.interleave, code, BatchLaunch{a, sh, (cudaStream_t)stream, false});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
 int ac_prepare_batch(const ScanShape& sh) {
     BatchArgs dummy{};
-    const int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{dummy, sh, nullptr, true});
+    int rc = dispatch(sh.interleave, sh.stride, BatchLaunch{dummy, sh, nullptr, true});
+    if (rc == 0 && sh.stride == 3) rc = dispatch(sh.interleave, 4u, BatchLaunch{dummy, sh, nullptr, true});
     return rc < 0 ? (int)cudaErrorInvalidValue : rc;
 }
 
