@@ -315,7 +315,7 @@ def run_plain(args, world, rank, local):
     desc_h = N.Text(host_packed.data_ptr(), n, N.AC_TEXT_PACKED2, 0)
     res_h = N.Result(raw_h.data_ptr(), cap, 0, cnt_h.data_ptr(), 0, 0, 0)
     k_e2e = max(1, min(args.steps, 5))
-    for _ in range(2):
+    for _ in range(3):
         lib.ac_scan(dfa.h, ctypes.byref(desc_h), ctypes.byref(res_h), ctypes.byref(opts), sp, None)
     torch.cuda.synchronize()
     barrier(world)
