@@ -659,6 +659,7 @@ def run_serving(args, seconds: float, warm_s: float):
         "sustained_gbases_s": round(bases_in_window / max(end - (start + warm_s), 1e-9) / 1e9, 3),
         "offered_gbases_s": round(float(lens[(t_arr >= warm_s) & (t_arr < horizon)].sum()) / window / 1e9, 3),
         "device_busy_gbases_s": round(st["gbases_per_s"], 3), "batches": st["batches_launched"],
+        "overflow_batches": st["overflow_batches"],
         "warmup_s": warm_s,
     }
 

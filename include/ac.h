@@ -438,6 +438,8 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> results on the host   */
     double busy_s;                          /* wall time with work in flight   */
     double gbases_per_s;                    /* bases_completed / busy_s / 1e9  */
+    uint64_t overflow_batches;              /* batches that outgrew their output reservation
+                                               and ran once more with the exact room        */
 } ac_serve_stats_t;
 
 int ac_serve_create(const ac_serve_opts* opts /* nullable */, ac_server** out);

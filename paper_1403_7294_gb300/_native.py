@@ -101,7 +101,7 @@ class ServeStats(ctypes.Structure):
         ("submitted", u64), ("completed", u64), ("rejected", u64), ("failed", u64),
         ("bases_completed", u64), ("batches_launched", u64), ("p50_ms", ctypes.c_double),
         ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-        ("busy_s", ctypes.c_double), ("gbases_per_s", ctypes.c_double),
+        ("busy_s", ctypes.c_double), ("gbases_per_s", ctypes.c_double), ("overflow_batches", u64),
     ]
 
 

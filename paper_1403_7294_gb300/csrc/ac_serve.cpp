@@ -14,8 +14,8 @@
 // Per-request results are exactly the stand-alone scan's: the batch writes
 // every occurrence with its text index, the worker splits them per request,
 // and per-keyword counts are the histogram of each request's occurrences. If
-// a batch overflows its reservation, every request of that batch is re-run
-// alone with an exactly sized buffer.
+// a batch overflows its reservation (its occurrence count is still exact),
+// the batch runs once more with exactly that much room.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,6 +91,7 @@ struct ac_server {
     std::vector<std::thread> workers;
     // stats
     uint64_t submitted = 0, completed = 0, rejected = 0, failed = 0, bases_completed = 0, batches = 0;
+    uint64_t overflow_batches = 0;  // batches run twice for want of output room
     std::vector<double> lat_ms;
     double busy_s = 0.0;
     Clock::time_point busy_since;
@@ -100,29 +101,6 @@ struct ac_server {
     void run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>& batch, PinnedBuf& stage,
                    PinnedBuf& results);
 };
-
-namespace {
-
-// Stand-alone scan of one request (overflow fallback): exact capacity.
-int scan_alone(const ac_dfa* dfa, Request& r, cudaStream_t st) {
-    ac_text t{r.bytes.data(), r.n, r.encoding, 0};
-    ac_result res;
-    std::memset(&res, 0, sizeof res);
-    res.counts = nullptr;
-    res.on_device = 0;
-    int s = ac_scan(dfa, &t, &res, nullptr, st, nullptr);  // counts the occurrences
-    if (s != AC_OK && s != AC_ERR_OVERFLOW) return s;
-    r.matches.resize(res.n_matches);
-    r.counts.assign(dfa->host.n_patterns, 0);
-    res.matches = r.matches.data();
-    res.capacity = res.n_matches;
-    res.counts = r.counts.data();
-    s = ac_scan(dfa, &t, &res, nullptr, st, nullptr);
-    r.n_matches = res.n_matches;
-    return s;
-}
-
-}  // namespace
 
 void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>& batch, PinnedBuf& stage,
                           PinnedBuf& results) {
@@ -144,6 +122,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     const uint64_t all = slot[B];
     const size_t packed_bytes = all / 4;
     int status = AC_OK;
+    bool overflowed = false;
     uint8_t* d_ascii = nullptr;
     uint32_t* d_packed = nullptr;
     ac_match* d_m = nullptr;
@@ -199,10 +178,21 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
         int s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
         nm = res.n_matches;
         if (s == AC_ERR_OVERFLOW) {
-            for (auto& r : batch)
-                if (r->status == AC_OK) r->status = scan_alone(dfa, *r, st);
-            nm = 0;
-        } else if (s != AC_OK) {
+            // more occurrences than reserved: the count is exact, so the batch runs once more with room for all
+            overflowed = true;
+            cudaFreeAsync(d_m, st);
+            d_m = nullptr;
+            if (cudaMallocAsync((void**)&d_m, std::max<uint64_t>(nm, 1) * sizeof(ac_match), st) != cudaSuccess) {
+                s = AC_ERR_OOM;
+            } else {
+                res.matches = d_m;
+                res.capacity = nm;
+                res.n_matches = 0;
+                s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
+                nm = res.n_matches;
+            }
+        }
+        if (s != AC_OK) {
             fail_all(s);
         } else {
             const size_t mb = nm * sizeof(ac_match);
@@ -242,6 +232,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     cudaStreamSynchronize(st);
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);
+    if (overflowed) overflow_batches++;
     for (auto& r : batch) {
         if (status != AC_OK && r->status == AC_OK) r->status = status;
         r->done = true;
@@ -427,6 +418,7 @@ extern "C" int ac_serve_stats(ac_server* s, ac_serve_stats_t* o) {
     o->failed = s->failed;
     o->bases_completed = s->bases_completed;
     o->batches_launched = s->batches;
+    o->overflow_batches = s->overflow_batches;
     double busy = s->busy_s;
     if (s->active_batches) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
     o->busy_s = busy;
