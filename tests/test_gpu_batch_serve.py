@@ -164,6 +164,35 @@ def test_serve_alone_equals_mix_equals_oracle():
         assert np.array_equal(alone[i][1], counts)
 
 
+def test_serve_batch_overflow_reruns_exactly():
+    """Requests far denser in occurrences than the server's output reservation:
+    each overflowing batch runs once more with exactly the room it needs, and
+    every request still gets its exact result."""
+    rng = random.Random(22)
+    pats = [b"AAAA", b"AAAAAA", b"ACAC", b"CACA", b"ACACACAC", b"GATTACA"]
+    d = acg.build(pats)
+    texts = []
+    for i in range(24):
+        n = rng.randint(2_000, 40_000)
+        parts, L = [], 0
+        while L < n:
+            unit = rng.choice([b"A" * rng.randint(5, 60), b"AC" * rng.randint(3, 40), rand_dna(rng, rng.randint(5, 50))])
+            parts.append(unit)
+            L += len(unit)
+        texts.append(b"".join(parts)[:n])
+    srv = acg.Server(n_streams=2, max_batch=8, match_capacity_per_base_x1000=1)
+    slot = srv.add_dfa(d)
+    tickets = [srv.submit(slot, t) for t in texts]
+    got = [srv.wait(tk, slot, capacity=1 << 16) for tk in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 0 and st["overflow_batches"] > 0
+    for t, (m, c, _) in zip(texts, got):
+        want, counts = oracle_canonical(pats, t)
+        assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:])
+        assert np.array_equal(c, counts)
+
+
 def test_serve_admission_and_errors():
     d = acg.build([b"ACGT"])
     srv = acg.Server(device_budget_bytes=1 << 20, n_streams=1, max_batch=4, max_queue=2)
