@@ -428,7 +428,9 @@ typedef struct {
     uint32_t n_streams;           /* concurrent batches on the device; 0 = 4               */
     uint32_t max_batch;           /* requests per launched batch; 0 = 256                  */
     uint32_t max_queue;           /* waiting requests before submit returns BUSY; 0 = 1<<16 */
-    uint32_t match_capacity_per_base_x1000; /* output reservation: capacity = n*x/1000 + 1024; 0 = 64 */
+    uint32_t match_capacity_per_base_x1000; /* output reservation per request: n*d + 1024 with d the
+                                               larger of x/1000 and twice the densest batch seen
+                                               for that dfa (occurrences per base); 0 = 64 */
 } ac_serve_opts;
 
 typedef struct {

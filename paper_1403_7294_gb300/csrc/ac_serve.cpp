@@ -10,7 +10,9 @@
 // meantime, so scans of different sizes overlap on the device.
 //
 // A request's device bytes: its packed text (n/4), its ASCII text if it came
-// as ASCII (n), and its output reservation (16 B per reserved occurrence).
+// as ASCII (n), and its output reservation (16 B per reserved occurrence). The
+// reservation per base is learned per dfa from the batches it has served
+// (twice the densest seen, decaying slowly), so batches rarely outgrow it.
 // Per-request results are exactly the stand-alone scan's: the batch writes
 // every occurrence with its text index, the worker splits them per request,
 // and per-keyword counts are the histogram of each request's occurrences. If
@@ -82,6 +84,9 @@ struct ac_server {
     std::condition_variable cv_work;  // workers: new requests / freed budget / stop
     std::condition_variable cv_done;  // waiters: completions
     std::vector<const ac_dfa*> dfas;
+    // learned occurrences per base of each dfa's requests: twice the densest
+    // batch seen, decaying slowly, so reservations rarely fall short
+    std::vector<double> density;
     std::deque<std::shared_ptr<Request>> pending;
     std::unordered_map<uint64_t, std::shared_ptr<Request>> by_ticket;
     uint64_t next_ticket = 1;
@@ -233,6 +238,10 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);
     if (overflowed) overflow_batches++;
+    if (status == AC_OK && all) {
+        double& dn = density[batch[0]->slot];
+        dn = std::max(dn * 0.999, 2.0 * (double)nm / (double)all);
+    }
     for (auto& r : batch) {
         if (status != AC_OK && r->status == AC_OK) r->status = status;
         r->done = true;
@@ -333,6 +342,7 @@ extern "C" int ac_serve_add_dfa(ac_server* s, const ac_dfa* dfa, uint32_t* slot)
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lk(s->mu);
     s->dfas.push_back(dfa);
+    s->density.push_back(0.0);
     *slot = (uint32_t)(s->dfas.size() - 1);
     return AC_OK;
 }
@@ -352,13 +362,14 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
     r->slot = slot;
     r->encoding = t->encoding;
     r->n = t->n_bases;
-    r->reserve = t->n_bases * s->opts.match_capacity_per_base_x1000 / 1000 + 1024;
     const uint64_t nb = t->encoding == AC_TEXT_ASCII ? t->n_bases : (t->n_bases + 15) / 16 * 4;
-    r->dev_bytes = round_up(t->n_bases, 64) / 4 + (t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : 0) +
-                   r->reserve * sizeof(ac_match);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (slot >= s->dfas.size()) return AC_ERR_NOT_FOUND;
+        const double per_base = std::max(s->opts.match_capacity_per_base_x1000 / 1000.0, s->density[slot]);
+        r->reserve = (uint64_t)((double)t->n_bases * per_base) + 1024;
+        r->dev_bytes = round_up(t->n_bases, 64) / 4 + (t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : 0) +
+                       r->reserve * sizeof(ac_match);
         if (s->stop || s->pending.size() >= s->opts.max_queue || r->dev_bytes > s->opts.device_budget_bytes) {
             s->rejected++;
             return AC_ERR_BUSY;
