@@ -87,13 +87,16 @@ def max_over_ranks(x: float, world: int) -> float:
 
 # DRAM traffic of the scan kernel per base of the genome workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of one launch over a
-# 1 Gbase slice of the same generator, the shape tuned for it); a 3 Gbase launch
-# is scaled by its bases (traffic grows with the text). It holds only for the
-# library sources it was taken from: the hash below; otherwise traffic is null.
-TRAFFIC_CAPTURE = {"workload": "genome", "sources_sha256": "21905a1ca8269290a87da36c5c0ac0a56c8f353f40bbea5d16bfc3a32086fd74",
+# 1 Gbase slice of the same generator); a 3 Gbase launch is scaled by its bases
+# (traffic grows with the text). It holds only for the same kernel and table
+# builder sources (hash), the same table sizes and the same launch shape;
+# otherwise traffic is null.
+TRAFFIC_CAPTURE = {"workload": "genome", "sources_sha256": "546b07e26af6fb427fad628e21a067a0e7b8845280c0c50d7394a260cb9dd2cc",
                    "bytes_per_base": (2.072646e9 + 2.594042e9) / 1e9,
+                   "shape": {"stride": 2, "threads": 1024, "interleave": 1, "hot_states": 0},
+                   "table2_bytes": 1462719 * 64, "table3_bytes": 1462719 * 256,
                    "capture": "profiles/scan_kernel_genome_1gbase_full.md"}
-TRAFFIC_SOURCES = ("ac_kernels.cu", "ac_internal.h", "ac_builder.cpp", "ac_api.cu", "ac_tune.cpp")
+TRAFFIC_SOURCES = ("ac_kernels.cu", "ac_builder.cpp")
 
 
 def library_sources_sha() -> str:
@@ -106,11 +109,12 @@ def library_sources_sha() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(workload: str, n_bases: int):
+def measured_traffic(workload: str, n_bases: int, shape: dict, info: dict):
     c = TRAFFIC_CAPTURE
-    if c["bytes_per_base"] is None or workload != c["workload"] or library_sources_sha() != c["sources_sha256"]:
-        return None
-    return int(round(c["bytes_per_base"] * n_bases))
+    same = (workload == c["workload"] and library_sources_sha() == c["sources_sha256"]
+            and all(shape.get(k) == v for k, v in c["shape"].items())
+            and info.get("table2_bytes") == c["table2_bytes"] and info.get("table3_bytes") == c["table3_bytes"])
+    return int(round(c["bytes_per_base"] * n_bases)) if same else None
 
 
 def load_peaks():
@@ -292,7 +296,9 @@ def run_plain(args, world, rank, local):
     achieved = alg_bytes / (scan_avg / 1e3) / 1e9
     out["roofline"] = {
         "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-        "frac": round(achieved / peak, 5), "traffic": measured_traffic(args.workload, n), "peak_source": peak_kind,
+        "frac": round(achieved / peak, 5), "peak_source": peak_kind,
+        "traffic": measured_traffic(args.workload, n, {k: getattr(stats, k) for k in ("stride", "threads", "interleave",
+                                                                                     "hot_states")}, dfa.info),
         "kernel": "scan_kernel", "kernel_ms": round(scan_avg, 4),
         "algorithmic_bytes": int(alg_bytes),
         "walked_bases_per_s": round(stats.bases_walked / (scan_avg / 1e3), 1),  # owned bases plus halo re-reads

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -149,6 +150,8 @@ extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint3
     const uint32_t flags = opts ? opts->flags : 0u;
     ac_dfa* d = new (std::nothrow) ac_dfa();
     if (!d) return AC_ERR_OOM;
+    static std::atomic<uint64_t> next_serial{1};
+    d->serial = next_serial++;
     int rc = ac_build_host(patterns, lens, n_patterns, (flags & AC_BUILD_FOLD_CASE) != 0,
                            (flags & AC_BUILD_NO_STRIDE2) == 0, opts ? opts->stride2_states : 0u,
                            (flags & AC_BUILD_NO_STRIDE3) == 0, opts ? opts->stride3_states : 0u,

@@ -72,6 +72,7 @@ struct ac_dfa {
     uint32_t* d_own_ent = nullptr;  // [2P] {keyword id, keyword length} per own entry
     uint64_t device_bytes = 0;
     double build_ms = 0.0;
+    uint64_t serial = 0;  // unique per built dfa in this process (tuned-shape reuse)
 };
 
 // ------------------------------------------------------------ launch shapes

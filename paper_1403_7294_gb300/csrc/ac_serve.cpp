@@ -131,6 +131,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     uint8_t* d_ascii = nullptr;
     uint32_t* d_packed = nullptr;
     ac_match* d_m = nullptr;
+    unsigned long long* d_cnt = nullptr;
     auto fail_all = [&](int s) { status = s; };
 
     // ---- stage: ASCII bytes padded with 'A', then packed words
@@ -180,6 +181,9 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
         res.matches = d_m;
         res.capacity = reserve;
         res.on_device = 1;
+        // a batch of one: the batch's counts are the request's counts (no histogram on the host)
+        if (B == 1 && cudaMallocAsync((void**)&d_cnt, (size_t)P * 8, st) != cudaSuccess) d_cnt = nullptr;
+        res.counts = (uint64_t*)d_cnt;
         int s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
         nm = res.n_matches;
         if (s == AC_ERR_OVERFLOW) {
@@ -201,13 +205,24 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             fail_all(s);
         } else {
             const size_t mb = nm * sizeof(ac_match);
-            if (!results.ensure(std::max<size_t>(mb, 16))) {
+            if (!results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
                 fail_all(AC_ERR_OOM);
             } else {
                 if (nm) cudaMemcpyAsync(results.p, d_m, mb, cudaMemcpyDeviceToHost, st);
+                if (d_cnt) cudaMemcpyAsync((uint8_t*)results.p + mb, d_cnt, (size_t)P * 8, cudaMemcpyDeviceToHost, st);
                 if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
             }
-            if (status == AC_OK) {
+            if (status == AC_OK && d_cnt) {
+                // one request: its occurrences already carry text index 0
+                Request& r = *batch[0];
+                if (r.status == AC_OK) {
+                    const ac_match* m = (const ac_match*)results.p;
+                    const uint64_t* c = (const uint64_t*)((const uint8_t*)results.p + mb);
+                    r.matches.assign(m, m + nm);
+                    r.counts.assign(c, c + P);
+                    r.n_matches = nm;
+                }
+            } else if (status == AC_OK) {
                 // split per request (counting sort by text index)
                 const ac_match* m = (const ac_match*)results.p;
                 std::vector<uint64_t> per(B, 0);
@@ -234,6 +249,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     if (d_ascii) cudaFreeAsync(d_ascii, st);
     if (d_packed) cudaFreeAsync(d_packed, st);
     if (d_m) cudaFreeAsync(d_m, st);
+    if (d_cnt) cudaFreeAsync(d_cnt, st);
     cudaStreamSynchronize(st);
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);

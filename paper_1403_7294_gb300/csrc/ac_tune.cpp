@@ -37,6 +37,7 @@ struct Entry {
 
 std::mutex g_mu;
 std::map<Key, Entry> g_cache;
+std::map<uint64_t, Entry> g_by_dfa;  // last shape tuned (or looked up) by ac_autotune per dfa serial
 bool g_loaded = false;
 
 uint32_t size_class(uint64_t x) { return x <= 1 ? 0u : (uint32_t)std::ceil(std::log2((double)x)); }
@@ -108,30 +109,21 @@ bool tuning_off() {
 bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out) {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_locked();
-    if (g_cache.empty()) return false;
-    const std::string dev = device_tag();
-    const unsigned sc = size_class(dfa->host.n_states), nc = size_class(n);
-    auto it = g_cache.find(Key{dev, sc, nc});
-    if (it == g_cache.end()) {
-        // no shape tuned for this text size: take the one tuned for the nearest
-        // text size on the same device and machine size (the table's placement
-        // is what the shape mostly reflects; chunks are recomputed for n)
-        unsigned best_d = ~0u;
-        for (auto jt = g_cache.begin(); jt != g_cache.end(); ++jt) {
-            if (std::get<0>(jt->first) != dev || std::get<1>(jt->first) != sc) continue;
-            const unsigned c = std::get<2>(jt->first);
-            const unsigned d = c > nc ? c - nc : nc - c;
-            if (d < best_d || (d == best_d && c > std::get<2>(it->first))) {
-                best_d = d;
-                it = jt;
-            }
-        }
-        if (it == g_cache.end()) return false;
+    const Entry* e = nullptr;
+    auto it = g_cache.find(Key{device_tag(), size_class(dfa->host.n_states), size_class(n)});
+    if (it != g_cache.end()) {
+        e = &it->second;
+    } else {
+        // no shape tuned for this machine size and text size: the shape last
+        // tuned for this very machine (on another text size) if there is one
+        auto jt = g_by_dfa.find(dfa->serial);
+        if (jt != g_by_dfa.end()) e = &jt->second;
     }
-    out->threads = it->second.threads;
-    out->interleave = it->second.interleave;
-    out->hot = it->second.hot;
-    out->stride = it->second.stride;
+    if (!e) return false;
+    out->threads = e->threads;
+    out->interleave = e->interleave;
+    out->hot = e->hot;
+    out->stride = e->stride;
     out->chunk = 0;
     return true;
 }
@@ -149,6 +141,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
         load_file_locked();
         auto it = g_cache.find(key);
         if (it != g_cache.end()) {
+            g_by_dfa[dfa->serial] = it->second;
             best->threads = it->second.threads;
             best->interleave = it->second.interleave;
             best->hot_states = (int32_t)it->second.hot;
@@ -235,6 +228,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_cache[key] = top;
+        g_by_dfa[dfa->serial] = top;
         append_file(key, top);
     }
     best->threads = top.threads;
