@@ -4,9 +4,12 @@
 // Layout in device memory
 //   delta    uint32[S][4]   row s = the 4 transitions of state s (16 B);
 //                           low bits next state, bit 31 "next state has output"
-//   delta2   uint32[S][16]  row s = the 16 two-base transitions (64 B);
+//   delta2   uint32[R2][16] row s = the 16 two-base transitions (64 B);
 //                           bit 31 "final state has output", bit 30 "state
 //                           after the first base has output"
+//   delta3   uint32[R3][64] row s = the 64 three-base transitions (256 B);
+//                           bits 31 / 30 / 29 "the state after the third /
+//                           second / first base has output"
 //   out_off  uint32[S+1], out_ent uint2[E]: output(s) as CSR, each entry
 //                          {keyword id, keyword length} (one 8-byte load gives
 //                          an occurrence's id and start position)
@@ -24,20 +27,21 @@
 // occurrence exactly once.
 //
 // Each thread walks `I` chunks at once (independent dependency chains: their
-// table lookups are in flight together), reading ST bases per lookup (ST = 1:
-// delta; ST = 2: delta2, half the dependent lookups per base). States
-// [0, hot) - the breadth-first prefix of the machine - are staged in shared
-// memory; the rest are read through L1/L2 with an evict-last policy, while
-// the streamed text uses evict-first.
+// table lookups are in flight together), reading one, two or three bases per
+// lookup (walk_any: ST = 1, 2 in lockstep; 3 with lanes on their own
+// schedules; 4 three bases in lockstep). States [0, hot) - the breadth-first
+// prefix of the machine - can be staged in shared memory; the rest are read
+// through L1/L2 with an evict-last policy, while the streamed text uses
+// evict-first.
 //
 // Emission: a step whose entry has a flag set lands on a state with output.
 // The warp votes; flagged, owned positions are appended to a per-warp event
-// queue in shared memory (ballot + popc); full queues are expanded 32 events
-// at a time (warp prefix sum, one atomicAdd on the occurrence counter per 32
-// events) one occurrence per lane: consecutive lanes read consecutive
-// output entries and write consecutive 16-byte occurrences (streaming
-// stores). A per-state hit counter feeds the exact per-keyword counts (kept
-// exact on overflow).
+// queue in shared memory (ballot + popc); a full queue of 64 events is
+// drained: per event the output-set bounds and the per-state hit counts, one
+// atomicAdd on the occurrence counter for the whole queue, then one
+// occurrence per lane - consecutive lanes read consecutive output entries and
+// write consecutive 16-byte occurrences (streaming stores). The per-state hit
+// counters feed the exact per-keyword counts (kept exact on overflow).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -173,8 +177,9 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, uint32_t lane
 
 // Expands the n <= QCAP queued hits of this warp; called by all 32 lanes
 // together, in two phases.
-//   Per event (lane l takes events l, l + 32, ...): the first-base lookup,
-//   the output-set bounds, the per-state hit counts (lanes holding the same
+//   Per event (lane l takes events l, l + 32, ...): the lookups that resolve
+//   a hit inside a multi-base step, the output-set bounds, the per-state hit
+//   counts (lanes holding the same
 //   state combine through __match_any_sync before one atomicAdd per distinct
 //   state), a warp prefix sum of the set sizes and one atomicAdd on the
 //   occurrence counter for the whole queue.
