@@ -310,6 +310,9 @@ def run_plain(args, world, rank, local):
         "kernel": "scan_kernel", "kernel_ms": round(scan_avg, 4),
         "algorithmic_bytes": int(alg_bytes),
         "walked_bases_per_s": round(stats.bases_walked / (scan_avg / 1e3), 1),  # owned bases plus halo re-reads
+        # one table lookup per step of `stride` bases (exact when every state has a row at that stride)
+        "table_lookups_per_s": round(stats.bases_walked / max(stats.stride, 1) / (scan_avg / 1e3), 1),
+        "kernel_ms_median": round(float(np.median(scan_ms)), 4), "kernel_ms_min": round(float(np.min(scan_ms)), 4),
     }
     if args.minimal:
         return out, None
@@ -903,7 +906,7 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload",
