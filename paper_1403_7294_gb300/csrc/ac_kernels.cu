@@ -533,7 +533,9 @@ __device__ __forceinline__ void walk3_free(const Chain (&ch)[I], const uint32_t*
 // three-base table covers every state: each step is one lookup for every
 // lane, so no lane waits on another, and the hits of a step are voted on
 // together. The text is read 48 bases (three words, sixteen steps) at a time
-// through L1: a lane's next groups come from the same cached line.
+// through L1: a lane's next groups come from the same cached line. The step
+// loop is not unrolled (its three append sites per step made the unrolled
+// body large enough to slow the emission-heavy regions).
 template <int I>
 __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                            const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
@@ -563,13 +565,12 @@ __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t*
             for (int v = 0; v < 3; ++v)
                 w[j][v] = (act && w0 + v < ch[j].nwords) ? ld_text1(ch[j].text + w0 + v, pol_txt) : 0u;
         }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int o = 6 * k, wi = o >> 5, sh = o & 31;  // the step's 6 bits within the 3 words
+#pragma unroll 1
+        for (uint32_t k = 0; k < 16; ++k) {
             uint32_t e[I], sp[I], sy[I];
 #pragma unroll
             for (int j = 0; j < I; ++j) {
-                sy[j] = (sh <= 26 ? (w[j][wi] >> sh) : __funnelshift_r(w[j][wi], w[j][wi + 1], sh)) & 63u;
+                sy[j] = w[j][0] & 63u;  // the next three bases
                 const uint32_t idx = (s[j] << 6) | sy[j];
                 e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta3 + idx, pol_tab);
             }
@@ -596,6 +597,12 @@ __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t*
                     const uint32_t m3 = __ballot_sync(FULL, h3);
                     if (m3) append(q, qn, m3, h3, ch[j].start + off + 2, 0u, s[j], ch[j].text_id, lt, em);
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < I; ++j) {  // move the window 6 bits on
+                w[j][0] = __funnelshift_r(w[j][0], w[j][1], 6);
+                w[j][1] = __funnelshift_r(w[j][1], w[j][2], 6);
+                w[j][2] >>= 6;
             }
         }
     }
