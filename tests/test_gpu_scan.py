@@ -120,7 +120,8 @@ def test_fuzz_vs_oracle(shape):
         assert_same(r, want, counts)
 
 
-def test_owned_ranges_concatenate_to_the_whole():
+@pytest.mark.parametrize("stride", [1, 2, 3])
+def test_owned_ranges_concatenate_to_the_whole(stride):
     rng = random.Random(5)
     text = rand_dna(rng, 30000)
     pats = [text[j : j + rng.randint(3, 10)] for j in rng.sample(range(29000), 50)] + [b"ACGTACGT"]
@@ -130,7 +131,7 @@ def test_owned_ranges_concatenate_to_the_whole():
     parts, counts = [], np.zeros(len(pats), np.int64)
     cuts = [0, 1, 17, 4096, 10000, 29999, 30000]
     for a, b in zip(cuts[:-1], cuts[1:]):
-        r = acg.scan(d, t, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), range_=(a, b))
+        r = acg.scan(d, t, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), range_=(a, b), stride=stride)
         c = r.canonical()
         ends = c[:, 1] + np.array([len(pats[p]) for p in c[:, 2]]) - 1
         assert np.all((ends >= a) & (ends < b))
