@@ -204,6 +204,25 @@ def make_workload(name: str, n_bases: int | None, device: str, rank: int):
     raise ValueError(name)
 
 
+def run_plain_configs(args, world, rank, local) -> dict:
+    """The other two plain-scan configurations (1 Mbase uniform text with 100
+    keywords; 256 Mbase chromosome with 10,000 keywords), timed like the main
+    line (autotuned, device-resident text, CUDA events), for the per-config table."""
+    import copy
+
+    res = {}
+    for name in ("small", "chromosome"):
+        sub = copy.copy(args)
+        sub.workload, sub.n_bases, sub.minimal = name, None, True
+        o, _ = run_plain(sub, world, rank, local)
+        res[name] = {"workload": o["config"]["workload"], "gbases_s": o["value"], "ms_per_step": o["ms_per_step"],
+                     "occurrences_per_step": o["config"]["occurrences_per_step"], "states": o["config"]["states"],
+                     "shape": o["config"]["shape"], "hbm_frac": o["roofline"]["frac"],
+                     "kernel_ms": o["roofline"]["kernel_ms"]}
+        torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------- plain scan
 
 
@@ -232,8 +251,12 @@ def run_plain(args, world, rank, local):
     ascii_prefix = None
     if not args.minimal and rank == 0:
         ascii_prefix = w.text.ascii[: min(n, 400_000_000)].cpu().numpy()
+    ascii_input = args.workload == "small"  # that configuration's input is uint8 ASCII: packing is in the step
+    ascii_dev = w.text.ascii if ascii_input else None
     del w.text.ascii
     torch.cuda.empty_cache()
+    # inputs smaller than L2 (129 MB) are flushed from it between timed steps
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if n // 4 < (256 << 20) else None
     P = len(w.patterns)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
@@ -241,7 +264,8 @@ def run_plain(args, world, rank, local):
     t0 = time.time()
     tuned = acg.autotune(dfa, packed, n)  # cached per (device, machine size, text size); untimed
     log(f"[bench] autotune {tuned} in {time.time() - t0:.1f}s")
-    desc = N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1)
+    desc = (N.Text(ascii_dev.data_ptr(), n, N.AC_TEXT_ASCII, 1) if ascii_input
+            else N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1))
     opts = N.ScanOpts()
     opts.hot_states = -1
     counts = torch.empty(P, dtype=torch.int64, device="cuda")
@@ -255,10 +279,15 @@ def run_plain(args, world, rank, local):
     res = N.Result(raw.data_ptr(), cap, 0, counts.data_ptr(), 1, 0, 0)
     stats = N.ScanStats()
 
+    call_ms = []  # device time of each whole ac_scan call (events inside it, on its stream)
+
     def step():
+        if flush is not None:
+            flush.fill_(1)  # evicts the text and tables from L2 (not inside the call's events)
         s = lib.ac_scan(dfa.h, ctypes.byref(desc), ctypes.byref(res), ctypes.byref(opts), sp, ctypes.byref(stats))
         if s != N.AC_OK:
             raise acg.AcError(s, "ac_scan")
+        call_ms.append(stats.total_ms)
         return stats.scan_ms
 
     for _ in range(args.warmup):
@@ -278,6 +307,8 @@ def run_plain(args, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    if flush is not None:  # the region between ev0 and ev1 holds the flushes too: count only the calls
+        ms = float(np.sum(call_ms[-args.steps:]))
     barrier(world)
     ms_max = max_over_ranks(ms, world)
     value = args.steps * n * world / (ms_max / 1e3) / 1e9
@@ -288,13 +319,18 @@ def run_plain(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {
             "workload": w.name, "n_bases": n, "patterns": P, "pattern_len": "20-25" if args.workload == "genome" else None,
-            "states": dfa.info["n_states"], "encoding": "2-bit packed, resident in HBM",
-            "occurrences_per_step": n_matches, "l2": f"inputs larger than L2 ({n // 4 / 1e6:.0f} MB packed text vs 129 MB L2)",
+            "states": dfa.info["n_states"],
+            "encoding": "uint8 ASCII resident in HBM, packed inside each step" if ascii_input else "2-bit packed, resident in HBM",
+            "occurrences_per_step": n_matches,
+            "l2": (f"L2 flushed between steps (512 MB write; {n // 4 / 1e6:.1f} MB packed text vs 129 MB L2), "
+                   "step time = device time of each ac_scan call") if flush is not None
+                  else f"inputs larger than L2 ({n // 4 / 1e6:.0f} MB packed text vs 129 MB L2)",
             "parallelism": f"replicas x{world}", "build_ms": round(dfa.info["build_ms"], 1),
-            "shape": {k: getattr(stats, k) for k in ("chunk", "threads", "interleave", "hot_states", "grid", "blocks_per_sm")},
+            "shape": {k: getattr(stats, k) for k in ("stride", "chunk", "threads", "interleave", "hot_states", "grid",
+                                                     "blocks_per_sm")},
             "autotuned": True,
         },
-        "gpu_launches": 2 * args.steps,  # scan kernel + count kernel per step
+        "gpu_launches": (3 if ascii_input else 2) * args.steps,  # (pack kernel +) scan kernel + count kernel per step
         "clocks": clk,
     }
     # roofline of the dominant kernel (the scan): algorithmic bytes per launch
@@ -998,6 +1034,7 @@ def main():
         if args.workload == "genome" and world == 1:
             out["batched"] = run_batched(args, max(3, args.steps))
             out["serving"] = run_serving(args, args.serve_seconds or 5.0, 1.0)
+            out["plain_configs"] = run_plain_configs(args, world, rank, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
