@@ -132,6 +132,10 @@ int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint6
 uint32_t ac_max_threads(uint32_t interleave, uint32_t stride = 1);
 // Whether kernels exist for an (interleave, stride) pair.
 bool ac_shape_compiled(uint32_t interleave, uint32_t stride);
+// Block size at or below which a shape runs the build with two blocks per SM
+// and 48 registers a thread (three bases per lookup, interleave 1); 0 where
+// there is no such build.
+uint32_t ac_wide_threads(uint32_t interleave, uint32_t stride);
 // Largest number of states a scan block of `threads` threads can stage in
 // shared memory (next to its per-warp event queues); rows are 16 B at
 // stride 1 and 64 B at stride 2.

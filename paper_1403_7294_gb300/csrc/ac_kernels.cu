@@ -326,6 +326,25 @@ struct MaxThreads {  // ST 1-4 as in walk_any
     static constexpr int value = I == 1 ? 1024 : (I <= 4 ? 512 : 256);
 };
 
+// Launch bounds of a kernel build. W = 0: one block of up to MaxThreads per
+// SM (no minimum asked of the compiler). W = 1, built for three bases per
+// lookup with one chain per lane only: at least two blocks of up to
+// kWideThreads per SM, so 48 registers a thread instead of 64 and 40 warps
+// in flight instead of 32 to cover the L2 misses of the 256-byte rows.
+constexpr uint32_t kWideThreads = 640;
+
+template <int I, int ST, int W>
+struct Bounds {
+    static constexpr int threads = W == 0 ? MaxThreads<I, ST>::value : (int)kWideThreads;
+    static constexpr int blocks = W == 0 ? 0 : 2;
+};
+
+// The build a launch of `threads` threads per block uses.
+template <int I, int ST>
+constexpr int wide_build(uint32_t threads) {
+    return (I == 1 && ST >= 3 && threads <= kWideThreads) ? 1 : 0;
+}
+
 // Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
 // call this together). q: this warp's event queue in shared memory.
 template <int I, int ST>
@@ -632,8 +651,8 @@ __device__ __forceinline__ void stage_hot(uint4* sm_rows, const uint32_t* table,
     __syncthreads();
 }
 
-template <int I, int ST>
-__global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
+template <int I, int ST, int W>
+__global__ void __launch_bounds__(Bounds<I, ST, W>::threads, Bounds<I, ST, W>::blocks) scan_kernel(ScanArgs a, uint32_t chunk, uint32_t hot, uint64_t n_chunks) {
     extern __shared__ uint4 sm_rows[];
     __shared__ Emit em;
     if (threadIdx.x == 0)
@@ -667,8 +686,8 @@ __global__ void __launch_bounds__(MaxThreads<I, ST>::value) scan_kernel(ScanArgs
 
 // Persistent batched scan: warps take 32*I work items at a time from a
 // device cursor; item -> (text, chunk) by binary search over item_prefix.
-template <int I, int ST>
-__global__ void __launch_bounds__(MaxThreads<I, ST>::value) batch_kernel(BatchArgs a, uint32_t hot) {
+template <int I, int ST, int W>
+__global__ void __launch_bounds__(Bounds<I, ST, W>::threads, Bounds<I, ST, W>::blocks) batch_kernel(BatchArgs a, uint32_t hot) {
     extern __shared__ uint4 sm_rows[];
     __shared__ Emit em;
     if (threadIdx.x == 0)
@@ -947,6 +966,10 @@ uint32_t ac_max_threads(uint32_t interleave, uint32_t stride) {
     }
 }
 
+uint32_t ac_wide_threads(uint32_t interleave, uint32_t stride) {
+    return (interleave == 1 && stride == 3) ? kWideThreads : 0u;
+}
+
 bool ac_shape_compiled(uint32_t interleave, uint32_t stride) {
     return (stride == 1 && (interleave == 1 || interleave == 2 || interleave == 4 || interleave == 8)) ||
            (stride == 2 && (interleave == 1 || interleave == 2 || interleave == 4)) ||
@@ -975,10 +998,17 @@ struct Occupancy {
     const ScanShape& sh;
     template <int I, int ST>
     int operator()() const {
+        if constexpr (I == 1 && ST >= 3) {
+            if (wide_build<I, ST>(sh.threads)) return blocks<I, ST, 1>();
+        }
+        return blocks<I, ST, 0>();
+    }
+    template <int I, int ST, int W>
+    int blocks() const {
         const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
-        if (set_smem(scan_kernel<I, ST>, smem) != 0) return 0;
+        if (set_smem(scan_kernel<I, ST, W>, smem) != 0) return 0;
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I, ST>, (int)sh.threads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<I, ST, W>, (int)sh.threads, smem) !=
             cudaSuccess)
             return 0;
         return nb;
@@ -992,10 +1022,17 @@ struct ScanLaunch {
     cudaStream_t st;
     template <int I, int ST>
     int operator()() const {
+        if constexpr (I == 1 && ST >= 3) {
+            if (wide_build<I, ST>(sh.threads)) return launch<I, ST, 1>();
+        }
+        return launch<I, ST, 0>();
+    }
+    template <int I, int ST, int W>
+    int launch() const {
         const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
-        int rc = set_smem(scan_kernel<I, ST>, smem);
+        int rc = set_smem(scan_kernel<I, ST, W>, smem);
         if (rc) return rc;
-        scan_kernel<I, ST><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks);
+        scan_kernel<I, ST, W><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks);
         return (int)cudaGetLastError();
     }
 };
@@ -1007,10 +1044,17 @@ struct BatchLaunch {
     bool prepare_only;
     template <int I, int ST>
     int operator()() const {
+        if constexpr (I == 1 && ST >= 3) {
+            if (wide_build<I, ST>(sh.threads)) return launch<I, ST, 1>();
+        }
+        return launch<I, ST, 0>();
+    }
+    template <int I, int ST, int W>
+    int launch() const {
         const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
-        int rc = set_smem(batch_kernel<I, ST>, smem);
+        int rc = set_smem(batch_kernel<I, ST, W>, smem);
         if (rc || prepare_only) return rc;
-        batch_kernel<I, ST><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);
+        batch_kernel<I, ST, W><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);
         return (int)cudaGetLastError();
     }
 };

@@ -174,7 +174,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     ac_match* d_m = nullptr;
     if (cudaMalloc(&d_m, std::max<uint64_t>(cap, 1) * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
 
-    const uint32_t threads_c[] = {256, 512, 768, 1024};
+    const uint32_t threads_c[] = {256, 512, 0, 768, 1024};  // 0: the two-blocks-per-SM build's size, if any
     const uint32_t inter_c[] = {1, 2, 4, 8};
     const uint32_t frac_c[] = {0, 1, 2, 4};  // shared-memory states: none, 1/4, 1/2, all that fit
     Entry top{0, 0, 0, 0, 1e30f};
@@ -183,9 +183,11 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
     const bool verbose = vb && vb[0] == '1';
     for (uint32_t sd = 1; sd <= 3; ++sd)
     for (uint32_t fr : frac_c)
-        for (uint32_t th : threads_c)
+        for (uint32_t th0 : threads_c)
             for (uint32_t il : inter_c) {
                 if ((sd == 2 && !dfa->d_delta2) || (sd == 3 && !dfa->d_delta3)) continue;  // table not built
+                const uint32_t th = th0 ? th0 : ac_wide_threads(il, sd);
+                if (th == 0) continue;
                 if (th > ac_max_threads(il, sd) || !ac_shape_compiled(il, sd)) continue;
                 const uint32_t hot = std::min(S, ac_max_hot_states(th, sd) * fr / 4);
                 if (fr && fr < 4 && hot >= S) continue;  // same as "all" for small machines

@@ -54,8 +54,9 @@ def packed_dev(texts):
 
 
 @pytest.mark.parametrize("form", ["packed_dev", "ascii_dev", "ascii_host", "packed_host"])
-@pytest.mark.parametrize("interleave,stride", [(1, 1), (4, 1), (1, 2), (2, 2), (1, 3), (2, 3)])
-def test_batch_vs_oracle(form, interleave, stride):
+@pytest.mark.parametrize("interleave,stride,threads",
+                         [(1, 1, 0), (4, 1, 0), (1, 2, 0), (2, 2, 0), (1, 3, 0), (2, 3, 0), (1, 3, 640), (1, 3, 256)])
+def test_batch_vs_oracle(form, interleave, stride, threads):
     texts, pats = batch_case(11)
     d = acg.build(pats)
     want, counts = oracle_batch(pats, texts)
@@ -70,7 +71,8 @@ def test_batch_vs_oracle(form, interleave, stride):
         enc = N.AC_TEXT_ASCII
     else:
         arg, enc = [np.frombuffer(t, np.uint8) if t else np.zeros(0, np.uint8) for t in texts], N.AC_TEXT_ASCII
-    r = acg.scan_batch(d, arg, encoding=enc, n_bases=lens, capacity=16, interleave=interleave, stride=stride)
+    r = acg.scan_batch(d, arg, encoding=enc, n_bases=lens, capacity=16, interleave=interleave, stride=stride,
+                       threads=threads)
     got = r.canonical()
     assert np.array_equal(got, want)
     assert r.counts.cpu().numpy().tolist() == counts.tolist()
@@ -90,13 +92,15 @@ def test_batch_equals_per_text_loop():
     assert np.array_equal(b, loop)
 
 
-@pytest.mark.parametrize("chunk,stride", [(0, 1), (64, 1), (1000, 1), (0, 2), (64, 2), (0, 3), (1000, 3)])
-def test_batch_plan_replays_exactly(chunk, stride):
+@pytest.mark.parametrize("chunk,stride,threads",
+                         [(0, 1, 0), (64, 1, 0), (1000, 1, 0), (0, 2, 0), (64, 2, 0), (0, 3, 0), (1000, 3, 0), (0, 3, 640)])
+def test_batch_plan_replays_exactly(chunk, stride, threads):
     texts, pats = batch_case(13, 100)
     d = acg.build(pats)
     want, counts = oracle_batch(pats, texts)
     pk = packed_dev(texts)
-    plan = acg.BatchPlan(d, pk, [len(t) for t in texts], capacity=len(want) + 10, chunk=chunk, stride=stride)
+    plan = acg.BatchPlan(d, pk, [len(t) for t in texts], capacity=len(want) + 10, chunk=chunk, stride=stride,
+                         threads=threads)
     for _ in range(3):  # replays reset their counters
         assert plan.run() == len(want)
         assert np.array_equal(plan.result().canonical(), want)

@@ -7,6 +7,7 @@ example, seeded fuzz over every launch shape the kernels offer (chunk sizes
 1, 2, 4, 8), owned ranges, host and device buffers, overflow, alphabet
 errors and the 1 Mbase uniform workload in full."""
 import random
+import re
 
 import numpy as np
 import pytest
@@ -79,7 +80,8 @@ def _cases(seed, k):
 
 SHAPES = ["default", "c1", "c2", "cLm1", "cL", "c97", "c4096", "cn", "hot0", "hot1", "i1", "i2", "i8",
           "s2", "s2i2", "s2i4", "s2hot0", "s2c1", "s2c97", "s1", "s2rows3", "s2rows40i2",
-          "s3", "s3i2", "s3hot0", "s3hot1", "s3c1", "s3c97", "s3rows3", "s3rows40i2"]
+          "s3", "s3i2", "s3hot0", "s3hot1", "s3c1", "s3c97", "s3rows3", "s3rows40i2",
+          "s3t640", "s3t256", "s3t640hot1", "s3rows3t640"]  # tN: N-thread blocks (two or more per SM)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -97,23 +99,18 @@ def test_fuzz_vs_oracle(shape):
         elif shape.startswith("i"):
             kw["interleave"] = int(shape[1:])
         elif shape.startswith("s"):  # two or three bases per lookup (s1: one, forced)
-            kw["stride"] = int(shape[1])
-            rest = shape[2:]
-            if rest.startswith("rows"):  # multi-base rows only for the shallowest states
-                r_, _, il = rest[4:].partition("i")
+            m = re.fullmatch(r"s(\d)(?:rows(\d+))?(?:t(\d+))?(?:i(\d+))?(?:hot(\d+))?(?:c(\d+))?", shape)
+            stride, rows, threads, il, hot, chunk = m.groups()
+            kw["stride"] = int(stride)
+            if rows:  # multi-base rows only for the shallowest states
                 if kw["stride"] == 3:  # R three-base rows, 2R two-base rows, one-base lookups beyond
-                    build_kw["stride3_states"] = int(r_)
-                    build_kw["stride2_states"] = 2 * int(r_)
+                    build_kw["stride3_states"] = int(rows)
+                    build_kw["stride2_states"] = 2 * int(rows)
                 else:
-                    build_kw["stride2_states"] = int(r_)
-                if il:
-                    kw["interleave"] = int(il)
-            elif rest.startswith("i"):
-                kw["interleave"] = int(rest[1:])
-            elif rest.startswith("hot"):
-                kw["hot_states"] = int(rest[3:])
-            elif rest.startswith("c"):
-                kw["chunk"] = int(rest[1:])
+                    build_kw["stride2_states"] = int(rows)
+            for key, v in (("threads", threads), ("interleave", il), ("hot_states", hot), ("chunk", chunk)):
+                if v:
+                    kw[key] = int(v)
         d = acg.build(pats, **build_kw)
         want, counts = oracle_canonical(pats, text)
         r = acg.scan(d, to_dev(text), capacity=4, **kw)  # tiny capacity: exercises the overflow retry
@@ -236,7 +233,7 @@ def test_autotune_then_exact():
     d = acg.build(pats)
     packed = acg.pack(to_dev(text))
     best = acg.autotune(d, packed, len(text))
-    assert best["interleave"] in (1, 2, 4, 8) and best["threads"] in (256, 512, 768, 1024)
+    assert best["interleave"] in (1, 2, 4, 8) and best["threads"] in (256, 512, 640, 768, 1024)
     assert best["stride"] in (1, 2, 3)
     want, counts = oracle_canonical(pats, text)
     r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), threads=best["threads"],

@@ -67,12 +67,14 @@ def test_genome_sampled_parity_and_invariants():
     b = torch.sort(_keys(r2.pos, r2.pattern_id))[0]
     assert torch.equal(a, b)
     del r2, b
-    # and three bases per lookup
-    r3 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, stride=3)
-    assert r3.n_matches == k
-    assert torch.equal(a, torch.sort(_keys(r3.pos, r3.pattern_id))[0])
-    assert torch.equal(r.counts, r3.counts)
-    del r3
+    # and three bases per lookup, in one 1024-thread block per SM and in two 640-thread blocks
+    for threads in (1024, 640):
+        r3 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, stride=3,
+                      threads=threads)
+        assert r3.n_matches == k
+        assert torch.equal(a, torch.sort(_keys(r3.pos, r3.pattern_id))[0])
+        assert torch.equal(r.counts, r3.counts)
+        del r3
     assert torch.equal(r.counts, acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=0,
                                           interleave=2, stride=1).counts)
     # sampled windows against the oracle
