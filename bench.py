@@ -91,9 +91,9 @@ def max_over_ranks(x: float, world: int) -> float:
 # (traffic grows with the text). It holds only for the same kernel and table
 # builder code (hash of the sources without comments), the same table sizes
 # and the same launch shape; otherwise traffic is null.
-TRAFFIC_CAPTURE = {"workload": "genome", "sources_sha256": "dce5f437dc9e021c89da8f6ebe56645a62b5553d00f74fbc2880d655be95a2f4",
-                   "bytes_per_base": (2.072492e9 + 2.593860e9) / 1e9,
-                   "shape": {"stride": 2, "threads": 1024, "interleave": 1, "hot_states": 0},
+TRAFFIC_CAPTURE = {"workload": "genome", "sources_sha256": "4c27887f82f0c2dcbbfda030ac2ad86fd32ff92f77d29dd88d487b89f8af6653",
+                   "bytes_per_base": (6.126702e9 + 2.629711e9) / 1e9,
+                   "shape": {"stride": 3, "threads": 640, "interleave": 1, "hot_states": 0},
                    "table2_bytes": 1462719 * 64, "table3_bytes": 1462719 * 256,
                    "capture": "profiles/scan_kernel_genome_1gbase_full.md"}
 TRAFFIC_SOURCES = ("ac_kernels.cu", "ac_builder.cpp")
@@ -213,7 +213,7 @@ def run_plain_configs(args, world, rank, local) -> dict:
     res = {}
     for name in ("small", "chromosome"):
         sub = copy.copy(args)
-        sub.workload, sub.n_bases, sub.minimal = name, None, True
+        sub.workload, sub.n_bases, sub.minimal, sub.shape = name, None, True, None
         o, _ = run_plain(sub, world, rank, local)
         res[name] = {"workload": o["config"]["workload"], "gbases_s": o["value"], "ms_per_step": o["ms_per_step"],
                      "occurrences_per_step": o["config"]["occurrences_per_step"], "states": o["config"]["states"],
@@ -261,13 +261,16 @@ def run_plain(args, world, rank, local):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    t0 = time.time()
-    tuned = acg.autotune(dfa, packed, n)  # cached per (device, machine size, text size); untimed
-    log(f"[bench] autotune {tuned} in {time.time() - t0:.1f}s")
-    desc = (N.Text(ascii_dev.data_ptr(), n, N.AC_TEXT_ASCII, 1) if ascii_input
-            else N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1))
     opts = N.ScanOpts()
     opts.hot_states = -1
+    if args.shape:  # a fixed launch shape instead of the tuned one
+        opts.stride, opts.threads, opts.interleave, opts.hot_states = (int(x) for x in args.shape.split(","))
+    else:
+        t0 = time.time()
+        tuned = acg.autotune(dfa, packed, n)  # cached per (device, machine size, text size); untimed
+        log(f"[bench] autotune {tuned} in {time.time() - t0:.1f}s")
+    desc = (N.Text(ascii_dev.data_ptr(), n, N.AC_TEXT_ASCII, 1) if ascii_input
+            else N.Text(packed.data_ptr(), n, N.AC_TEXT_PACKED2, 1))
     counts = torch.empty(P, dtype=torch.int64, device="cuda")
     # size the occurrence buffer with one counting pass
     r = N.Result(None, 0, 0, counts.data_ptr(), 1, 0, 0)
@@ -328,7 +331,7 @@ def run_plain(args, world, rank, local):
             "parallelism": f"replicas x{world}", "build_ms": round(dfa.info["build_ms"], 1),
             "shape": {k: getattr(stats, k) for k in ("stride", "chunk", "threads", "interleave", "hot_states", "grid",
                                                      "blocks_per_sm")},
-            "autotuned": True,
+            "autotuned": not args.shape,
         },
         "gpu_launches": (3 if ascii_input else 2) * args.steps,  # (pack kernel +) scan kernel + count kernel per step
         "clocks": clk,
@@ -953,6 +956,8 @@ def main():
                     help="cpu-sweep: bases of the genome text each thread count scans")
     ap.add_argument("--n-bases", type=int, default=None)
     ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
+    ap.add_argument("--shape", default=None,
+                    help="plain workloads: fixed launch shape 'stride,threads,interleave,hot_states' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=None)
     ap.add_argument("--uniform-patterns", action="store_true",
                     help="replace the keywords by uniform random ones of the same shape (walk-only ceiling)")
