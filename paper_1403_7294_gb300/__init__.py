@@ -473,22 +473,27 @@ class Server:
                 return None
             raise
 
-    def wait(self, ticket: int, slot: int, capacity: int = 1 << 16, timeout_us: int = -1):
-        """Returns (matches (k,2) int64 numpy [pos, pid], counts int64[P], n_matches)."""
-        cap = capacity
+    def wait(self, ticket: int, slot: int, capacity: int | None = None, timeout_us: int = -1):
+        """Returns (matches (k,2) int64 numpy [pos, pid], counts int64[P], n_matches).
+
+        capacity None: the exact count is asked for first (a wait with no room
+        reports it and keeps the ticket), so the occurrences are copied once,
+        into an array of exactly that size. An int: that much room is tried
+        first, and the exact size only on overflow; the array returned is then
+        the first n_matches rows of the one allocated. Served occurrences carry
+        text index 0, so column 1 is the keyword id as it stands."""
+        cap = 0 if capacity is None else int(capacity)
         for _ in range(2):
             raw = np.empty((max(cap, 1), 2), dtype=np.int64)
             cnt = np.empty(self._npat[slot], dtype=np.int64)
-            r = N.Result(raw.ctypes.data, cap, 0, cnt.ctypes.data, 0, 0, 0)
+            r = N.Result(raw.ctypes.data if cap else None, cap, 0, cnt.ctypes.data, 0, 0, 0)
             st = lib().ac_serve_wait(self.h, ticket, ctypes.byref(r), timeout_us)
             if st == N.AC_ERR_OVERFLOW:  # the ticket stays valid: retry with the exact size
                 cap = int(r.n_matches)
                 continue
             N.check(st, "ac_serve_wait")
             k = int(r.n_matches)
-            m = raw[:k].copy()
-            m[:, 1] &= 0xFFFFFFFF
-            return m, cnt, k
+            return raw[:k], cnt, k
         raise AssertionError("unreachable")
 
     def stats(self) -> dict:
