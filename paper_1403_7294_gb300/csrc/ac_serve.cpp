@@ -57,6 +57,30 @@ struct Request {
 
 uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
 
+// High bit of each byte of the result set iff that byte of v is zero (exact:
+// the low seven bits are summed with 0x7f inside the byte, so no carry
+// crosses into the next byte).
+inline uint64_t zero_bytes(uint64_t v) {
+    constexpr uint64_t lo7 = 0x7f7f7f7f7f7f7f7full;
+    return ~(((v & lo7) + lo7) | v | lo7);
+}
+
+// Whether every byte is one of A, C, G, T, eight bytes per step.
+bool all_acgt(const uint8_t* b, uint64_t n) {
+    constexpr uint64_t ones = 0x0101010101010101ull, high = 0x8080808080808080ull;
+    uint64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t x;
+        std::memcpy(&x, b + i, 8);
+        const uint64_t ok = zero_bytes(x ^ (ones * 'A')) | zero_bytes(x ^ (ones * 'C')) |
+                            zero_bytes(x ^ (ones * 'G')) | zero_bytes(x ^ (ones * 'T'));
+        if (ok != high) return false;
+    }
+    for (; i < n; ++i)
+        if (b[i] != 'A' && b[i] != 'C' && b[i] != 'G' && b[i] != 'T') return false;
+    return true;
+}
+
 struct PinnedBuf {
     void* p = nullptr;
     size_t cap = 0;
@@ -369,11 +393,8 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
     if (t->encoding != AC_TEXT_ASCII && t->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (t->n_bases && !t->data) return AC_ERR_INVALID_ARG;
     if (t->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
-    if (t->encoding == AC_TEXT_ASCII) {  // reject bad input before it is queued
-        const uint8_t* b = (const uint8_t*)t->data;
-        for (uint64_t i = 0; i < t->n_bases; ++i)
-            if (b[i] != 'A' && b[i] != 'C' && b[i] != 'G' && b[i] != 'T') return AC_ERR_ALPHABET;
-    }
+    // reject bad input before it is queued
+    if (t->encoding == AC_TEXT_ASCII && !all_acgt((const uint8_t*)t->data, t->n_bases)) return AC_ERR_ALPHABET;
     auto r = std::make_shared<Request>();
     r->slot = slot;
     r->encoding = t->encoding;

@@ -217,6 +217,29 @@ def test_serve_admission_and_errors():
     srv.close()
 
 
+def test_serve_submit_alphabet_check():
+    """Submit rejects an ASCII text with any byte other than A, C, G, T, wherever it sits
+    (eight bytes are checked per step, then the tail one by one), and queues good texts."""
+    d = acg.build([b"ACGT"])
+    srv = acg.Server(n_streams=1)
+    slot = srv.add_dfa(d)
+    rng = random.Random(23)
+    for n in (1, 7, 8, 9, 15, 16, 17, 31, 40):
+        for pos in range(n):
+            for v in (ord("a"), ord("N"), ord("B"), ord("U"), 0x00, 0xC1, 0xFF, ord("A") | 0x80):
+                t = bytearray(rand_dna(rng, n))
+                t[pos] = v
+                with pytest.raises(acg.AcError) as e:
+                    srv.submit(slot, bytes(t))
+                assert e.value.status == N.AC_ERR_ALPHABET, (n, pos, v)
+    good = rand_dna(rng, 100_003)
+    m, c, k = srv.wait(srv.submit(slot, good), slot)
+    want, counts = oracle_canonical([b"ACGT"], good)
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and c.tolist() == counts.tolist()
+    assert srv.stats()["failed"] == 0
+    srv.close()
+
+
 def test_serve_wait_timeout_keeps_ticket():
     d = acg.build([b"ACGT"])
     srv = acg.Server(n_streams=1)
