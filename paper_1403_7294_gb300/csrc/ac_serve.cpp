@@ -39,6 +39,60 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Pinned host blocks reused across batches: a block stays with the request
+// whose results it holds until the request is forgotten, then goes back to
+// the free list (beyond kKeepFree free bytes it is released).
+class PinnedPool {
+  public:
+    struct Block {
+        void* p = nullptr;
+        size_t cap = 0;
+        PinnedPool* pool = nullptr;
+        ~Block() { pool->put(p, cap); }
+    };
+    ~PinnedPool() {
+        for (auto& f : free_) cudaFreeHost(f.second);
+    }
+    // a block of at least `bytes` (sizes are powers of two from 1 MiB), or null
+    std::shared_ptr<Block> get(size_t bytes) {
+        size_t cap = (size_t)1 << 20;
+        while (cap < bytes) cap <<= 1;
+        void* p = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto it = free_.find(cap);
+            if (it != free_.end()) {
+                p = it->second;
+                free_.erase(it);
+                free_bytes_ -= cap;
+            }
+        }
+        if (!p && cudaMallocHost(&p, cap) != cudaSuccess) return nullptr;
+        auto b = std::make_shared<Block>();
+        b->p = p;
+        b->cap = cap;
+        b->pool = this;
+        return b;
+    }
+
+  private:
+    static constexpr size_t kKeepFree = (size_t)1 << 30;
+    void put(void* p, size_t cap) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (free_bytes_ + cap <= kKeepFree) {
+                free_.emplace(cap, p);
+                free_bytes_ += cap;
+                return;
+            }
+        }
+        cudaFreeHost(p);
+    }
+    std::mutex mu_;
+    std::multimap<size_t, void*> free_;
+    size_t free_bytes_ = 0;
+};
+
 struct Request {
     uint64_t ticket = 0;
     uint32_t slot = 0;
@@ -53,9 +107,21 @@ struct Request {
     std::vector<ac_match> matches;
     std::vector<uint64_t> counts;
     uint64_t n_matches = 0;
+    // a batch of one leaves its results in a pinned block instead: n_matches
+    // occurrences, then the counts
+    std::shared_ptr<PinnedPool::Block> block;
+    const ac_match* match_data() const { return block ? (const ac_match*)block->p : matches.data(); }
+    const uint64_t* count_data() const {
+        return block ? (const uint64_t*)((const uint8_t*)block->p + n_matches * sizeof(ac_match)) : counts.data();
+    }
+    size_t n_counts = 0;
 };
 
 uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
+
+// Results of a one-request batch at least this large stay in a pinned block
+// handed to the request; smaller ones are copied out of the worker's buffer.
+constexpr size_t kHandoffBytes = (size_t)1 << 20;
 
 // High bit of each byte of the result set iff that byte of v is zero (exact:
 // the low seven bits are summed with 0x7f inside the byte, so no carry
@@ -102,6 +168,7 @@ struct PinnedBuf {
 }  // namespace
 
 struct ac_server {
+    PinnedPool pool;  // result blocks of one-request batches (destroyed last)
     ac_serve_opts opts{};
     int device = 0;
     std::mutex mu;
@@ -229,26 +296,43 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             fail_all(s);
         } else {
             const size_t mb = nm * sizeof(ac_match);
-            if (!results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
+            // one request with many occurrences: they (with text index 0 already)
+            // and the batch's counts, which are the request's, land in a pinned
+            // block the request keeps until it is waited for; no copy on the host
+            const bool handoff = d_cnt && mb >= kHandoffBytes;
+            std::shared_ptr<PinnedPool::Block> blk;
+            void* dst = nullptr;
+            if (handoff) {
+                blk = pool.get(mb + (size_t)P * 8);
+                dst = blk ? blk->p : nullptr;
+            } else if (results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
+                dst = results.p;
+            }
+            if (!dst) {
                 fail_all(AC_ERR_OOM);
             } else {
-                if (nm) cudaMemcpyAsync(results.p, d_m, mb, cudaMemcpyDeviceToHost, st);
-                if (d_cnt) cudaMemcpyAsync((uint8_t*)results.p + mb, d_cnt, (size_t)P * 8, cudaMemcpyDeviceToHost, st);
+                if (nm) cudaMemcpyAsync(dst, d_m, mb, cudaMemcpyDeviceToHost, st);
+                if (d_cnt) cudaMemcpyAsync((uint8_t*)dst + mb, d_cnt, (size_t)P * 8, cudaMemcpyDeviceToHost, st);
                 if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
             }
             if (status == AC_OK && d_cnt) {
-                // one request: its occurrences already carry text index 0
                 Request& r = *batch[0];
                 if (r.status == AC_OK) {
-                    const ac_match* m = (const ac_match*)results.p;
-                    const uint64_t* c = (const uint64_t*)((const uint8_t*)results.p + mb);
-                    r.matches.assign(m, m + nm);
-                    r.counts.assign(c, c + P);
+                    if (handoff) {
+                        r.block = std::move(blk);
+                    } else {
+                        const ac_match* m = (const ac_match*)dst;
+                        const uint64_t* c = (const uint64_t*)((const uint8_t*)dst + mb);
+                        r.matches.assign(m, m + nm);
+                        r.counts.assign(c, c + P);
+                    }
                     r.n_matches = nm;
+                    r.n_counts = P;
                 }
-            } else if (status == AC_OK) {
+            }
+            if (status == AC_OK && !d_cnt) {
                 // split per request (counting sort by text index)
-                const ac_match* m = (const ac_match*)results.p;
+                const ac_match* m = (const ac_match*)dst;
                 std::vector<uint64_t> per(B, 0);
                 for (uint64_t k = 0; k < nm; ++k) per[m[k].text_id]++;
                 for (size_t i = 0; i < B; ++i) {
@@ -258,6 +342,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
                     r.matches.reserve(per[i]);
                     r.counts.assign(P, 0);
                     r.n_matches = per[i];
+                    r.n_counts = P;
                 }
                 for (uint64_t k = 0; k < nm; ++k) {
                     Request& r = *batch[m[k].text_id];
@@ -451,8 +536,8 @@ extern "C" int ac_serve_wait(ac_server* s, uint64_t ticket, ac_result* res, int6
         s->by_ticket.erase(ticket);
     }
     if (r->status != AC_OK) return r->status;
-    if (r->n_matches) std::memcpy(res->matches, r->matches.data(), r->n_matches * sizeof(ac_match));
-    if (res->counts && !r->counts.empty()) std::memcpy(res->counts, r->counts.data(), r->counts.size() * 8);
+    if (r->n_matches) std::memcpy(res->matches, r->match_data(), r->n_matches * sizeof(ac_match));
+    if (res->counts && r->n_counts) std::memcpy(res->counts, r->count_data(), r->n_counts * 8);
     return AC_OK;
 }
 

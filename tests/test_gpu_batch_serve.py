@@ -197,6 +197,40 @@ def test_serve_batch_overflow_reruns_exactly():
         assert np.array_equal(c, counts)
 
 
+def test_serve_large_results_handed_over():
+    """Requests with 1 MB or more of occurrences (65,536+) keep their results in a pinned
+    block until they are waited for: results equal the oracle's whether waited at once,
+    out of order, with a too-small first capacity, or (one of them) never, and blocks
+    are reused across requests."""
+    rng = random.Random(24)
+    pats = [b"A", b"AA", b"AC", b"CA", b"ACGT"]
+    d = acg.build(pats)
+    srv = acg.Server(n_streams=2, max_batch=1)  # batches of one request
+    slot = srv.add_dfa(d)
+    texts = []
+    for i in range(8):
+        n = rng.randint(150_000, 400_000)
+        texts.append(bytes(rng.choice(b"AAAAACGT") for _ in range(n)))
+    texts.append(b"ACGT" * 10)  # a small result among them
+    tickets = [srv.submit(slot, t) for t in texts]
+    order = list(range(len(texts) - 1))
+    rng.shuffle(order)
+    for j, i in enumerate(order):
+        m, c, k = srv.wait(tickets[i], slot, capacity=(1000 if j % 2 else None))
+        want, counts = oracle_canonical(pats, texts[i])
+        assert k == len(want) and k >= 65_536
+        assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:])
+        assert np.array_equal(c, counts)
+    again = srv.submit(slot, texts[0])  # a block back from the pool
+    m, c, k = srv.wait(again, slot)
+    want, counts = oracle_canonical(pats, texts[0])
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and np.array_equal(c, counts)
+    srv.submit(slot, texts[1])  # left unclaimed: its block goes back when the server closes
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 0
+
+
 def test_serve_admission_and_errors():
     d = acg.build([b"ACGT"])
     srv = acg.Server(device_budget_bytes=1 << 20, n_streams=1, max_batch=4, max_queue=2)
