@@ -39,9 +39,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// Pinned host blocks reused across batches: a block stays with the request
-// whose results it holds until the request is forgotten, then goes back to
-// the free list (beyond kKeepFree free bytes it is released).
+// Pinned host blocks reused across requests: a block stays with the request
+// whose text or results it holds until the request is forgotten, then goes
+// back to the free list (beyond kKeepFree free bytes it is released).
 class PinnedPool {
   public:
     struct Block {
@@ -67,7 +67,7 @@ class PinnedPool {
                 free_bytes_ -= cap;
             }
         }
-        if (!p && cudaMallocHost(&p, cap) != cudaSuccess) return nullptr;
+        if (!p && cudaHostAlloc(&p, cap, cudaHostAllocPortable) != cudaSuccess) return nullptr;  // any thread's context
         auto b = std::make_shared<Block>();
         b->p = p;
         b->cap = cap;
@@ -99,6 +99,10 @@ struct Request {
     int32_t encoding = AC_TEXT_ASCII;
     uint64_t n = 0;
     std::vector<uint8_t> bytes;  // ASCII bytes or packed words
+    // a text of kHandoffBytes or more is copied at submit into a pinned block
+    // instead (ASCII padded with 'A' to a multiple of 64), which the worker
+    // copies to the device directly
+    std::shared_ptr<PinnedPool::Block> text_block;
     uint64_t reserve = 0;        // occurrences reserved
     uint64_t dev_bytes = 0;
     Clock::time_point t_submit, t_done;
@@ -119,28 +123,29 @@ struct Request {
 
 uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
 
-// Results of a one-request batch at least this large stay in a pinned block
-// handed to the request; smaller ones are copied out of the worker's buffer.
+// Texts at least this large are held in pinned blocks from submit on, and the
+// results of a one-request batch at least this large stay in a pinned block
+// handed to the request; smaller ones go through the worker's buffers.
 constexpr size_t kHandoffBytes = (size_t)1 << 20;
 
-// High bit of each byte of the result set iff that byte of v is zero (exact:
-// the low seven bits are summed with 0x7f inside the byte, so no carry
-// crosses into the next byte).
-inline uint64_t zero_bytes(uint64_t v) {
-    constexpr uint64_t lo7 = 0x7f7f7f7f7f7f7f7full;
-    return ~(((v & lo7) + lo7) | v | lo7);
-}
+// Whether every byte is one of A, C, G, T: 64 bytes per step through the
+// compiler's generic 16-byte vectors (no target-specific code; the host
+// compiler maps them to the machine's SIMD registers), the tail byte by byte.
+typedef uint8_t v16u8 __attribute__((vector_size(16)));
+typedef int8_t v16i8 __attribute__((vector_size(16)));
 
-// Whether every byte is one of A, C, G, T, eight bytes per step.
 bool all_acgt(const uint8_t* b, uint64_t n) {
-    constexpr uint64_t ones = 0x0101010101010101ull, high = 0x8080808080808080ull;
     uint64_t i = 0;
-    for (; i + 8 <= n; i += 8) {
-        uint64_t x;
-        std::memcpy(&x, b + i, 8);
-        const uint64_t ok = zero_bytes(x ^ (ones * 'A')) | zero_bytes(x ^ (ones * 'C')) |
-                            zero_bytes(x ^ (ones * 'G')) | zero_bytes(x ^ (ones * 'T'));
-        if (ok != high) return false;
+    for (; i + 64 <= n; i += 64) {
+        v16i8 bad = {};
+        for (int k = 0; k < 4; ++k) {
+            v16u8 x;
+            std::memcpy(&x, b + i + 16 * k, 16);
+            bad |= (x != 'A') & (x != 'C') & (x != 'G') & (x != 'T');  // lanes: -1 where not a base
+        }
+        uint64_t w[2];
+        std::memcpy(w, &bad, 16);
+        if (w[0] | w[1]) return false;
     }
     for (; i < n; ++i)
         if (b[i] != 'A' && b[i] != 'C' && b[i] != 'G' && b[i] != 'T') return false;
@@ -225,13 +230,15 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     unsigned long long* d_cnt = nullptr;
     auto fail_all = [&](int s) { status = s; };
 
-    // ---- stage: ASCII bytes padded with 'A', then packed words
+    // ---- stage: ASCII bytes padded with 'A', then packed words (texts held in
+    // pinned blocks are not staged: they are copied to the device from there)
     if (!stage.ensure(std::max<size_t>(ascii_bases + packed_bytes, 16))) fail_all(AC_ERR_OOM);
+    uint8_t* h_ascii = (uint8_t*)stage.p;
+    uint8_t* h_packed = h_ascii + ascii_bases;
     if (status == AC_OK) {
-        uint8_t* h_ascii = (uint8_t*)stage.p;
-        uint8_t* h_packed = h_ascii + ascii_bases;
         for (size_t i = 0; i < B; ++i) {
             Request& r = *batch[i];
+            if (r.text_block) continue;
             if (r.encoding == AC_TEXT_ASCII) {
                 std::memcpy(h_ascii + slot[i], r.bytes.data(), r.n);
                 std::memset(h_ascii + slot[i] + r.n, 'A', slot[i + 1] - slot[i] - r.n);
@@ -246,10 +253,28 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             fail_all(AC_ERR_OOM);
     }
     if (status == AC_OK) {
-        if (ascii_bases) cudaMemcpyAsync(d_ascii, stage.p, ascii_bases, cudaMemcpyHostToDevice, st);
-        if (all > ascii_bases)
-            cudaMemcpyAsync((uint8_t*)d_packed + ascii_bases / 4, (uint8_t*)stage.p + ascii_bases,
-                            (all - ascii_bases) / 4, cudaMemcpyHostToDevice, st);
+        auto h2d = [&](void* d, const void* h, size_t bytes) {
+            if (bytes) cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
+        };
+        // ASCII slots: runs of staged ones, and each pinned text (with its padding) on its own
+        uint64_t run = 0;  // first base of the current run of staged slots
+        for (size_t i = 0; i < B && batch[i]->encoding == AC_TEXT_ASCII; ++i) {
+            if (!batch[i]->text_block) continue;
+            h2d(d_ascii + run, h_ascii + run, slot[i] - run);
+            h2d(d_ascii + slot[i], batch[i]->text_block->p, slot[i + 1] - slot[i]);
+            run = slot[i + 1];
+        }
+        h2d(d_ascii + run, h_ascii + run, ascii_bases - run);
+        // packed slots (after the ASCII ones), the same way
+        run = ascii_bases;
+        for (size_t i = 0; i < B; ++i) {
+            const Request& r = *batch[i];
+            if (r.encoding == AC_TEXT_ASCII || !r.text_block) continue;
+            h2d((uint8_t*)d_packed + run / 4, h_packed + (run - ascii_bases) / 4, (slot[i] - run) / 4);
+            h2d((uint8_t*)d_packed + slot[i] / 4, r.text_block->p, (r.n + 15) / 16 * 4);
+            run = slot[i + 1];
+        }
+        h2d((uint8_t*)d_packed + run / 4, h_packed + (run - ascii_bases) / 4, (all - run) / 4);
         if (ascii_bases) {
             uint64_t bad = ~0ull;
             int s = ac_pack(d_ascii, ascii_bases, d_packed, 0, &bad, st);
@@ -369,6 +394,8 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     }
     for (auto& r : batch) {
         if (status != AC_OK && r->status == AC_OK) r->status = status;
+        r->text_block.reset();  // the text is on the device no longer: its host copy goes now
+        std::vector<uint8_t>().swap(r->bytes);
         r->done = true;
         r->t_done = now;
         in_flight_bytes -= r->dev_bytes;
@@ -498,7 +525,15 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
         }
     }
     try {
-        r->bytes.assign((const uint8_t*)t->data, (const uint8_t*)t->data + nb);
+        if (nb >= kHandoffBytes) {
+            const uint64_t held = t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : nb;
+            r->text_block = s->pool.get(held);
+            if (!r->text_block) return AC_ERR_OOM;
+            std::memcpy(r->text_block->p, t->data, nb);
+            std::memset((uint8_t*)r->text_block->p + nb, 'A', held - nb);
+        } else {
+            r->bytes.assign((const uint8_t*)t->data, (const uint8_t*)t->data + nb);
+        }
     } catch (const std::bad_alloc&) {
         return AC_ERR_OOM;
     }

@@ -231,6 +231,44 @@ def test_serve_large_results_handed_over():
     assert st["failed"] == 0
 
 
+@pytest.mark.parametrize("form", ["ascii", "packed"])
+def test_serve_large_texts_pinned_at_submit(form):
+    """Texts of 1 MB or more are held in pinned blocks from submit on and copied to the
+    device from there, between runs of small staged texts of the same batch (odd lengths,
+    ASCII or packed); every request gets the oracle's result."""
+    rng = random.Random(25)
+    src = rand_dna(rng, 3_000_000) * 2
+    pats = [src[j : j + rng.randint(8, 16)] for j in rng.sample(range(2_999_000), 300)]
+    d = acg.build(pats)
+    srv = acg.Server(n_streams=2, max_batch=16)
+    slot = srv.add_dfa(d)
+    reqs = []
+    for i in range(24):
+        if i % 2 == 0:
+            n = rng.randint(1, 5000)
+        elif form == "ascii":
+            n = rng.randint(1_100_000, 2_900_000)  # 1 byte a base
+        else:
+            n = rng.randint(4_300_000, 5_000_000)  # 16 bases a 4-byte word: over 1 MB of words
+        off = rng.randint(0, len(src) - n)
+        reqs.append(src[off : off + n])
+    tickets = []
+    for t in reqs:
+        if form == "packed":
+            pk = acg.pack(torch.from_numpy(np.frombuffer(t, np.uint8).copy()).to(DEV)).cpu().numpy()
+            tickets.append(srv.submit(slot, pk, encoding=N.AC_TEXT_PACKED2, n_bases=len(t)))
+        else:
+            tickets.append(srv.submit(slot, t))
+    for tk, t in zip(tickets, reqs):
+        m, c, k = srv.wait(tk, slot)
+        want, counts = oracle_canonical(pats, t)
+        assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:])
+        assert np.array_equal(c, counts)
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 0
+
+
 def test_serve_admission_and_errors():
     d = acg.build([b"ACGT"])
     srv = acg.Server(device_budget_bytes=1 << 20, n_streams=1, max_batch=4, max_queue=2)
@@ -253,12 +291,12 @@ def test_serve_admission_and_errors():
 
 def test_serve_submit_alphabet_check():
     """Submit rejects an ASCII text with any byte other than A, C, G, T, wherever it sits
-    (eight bytes are checked per step, then the tail one by one), and queues good texts."""
+    (64 bytes are checked per step, then the tail one by one), and queues good texts."""
     d = acg.build([b"ACGT"])
     srv = acg.Server(n_streams=1)
     slot = srv.add_dfa(d)
     rng = random.Random(23)
-    for n in (1, 7, 8, 9, 15, 16, 17, 31, 40):
+    for n in (1, 7, 8, 9, 15, 16, 17, 31, 40, 63, 64, 65, 127, 128, 129, 200):
         for pos in range(n):
             for v in (ord("a"), ord("N"), ord("B"), ord("U"), 0x00, 0xC1, 0xFF, ord("A") | 0x80):
                 t = bytearray(rand_dna(rng, n))
