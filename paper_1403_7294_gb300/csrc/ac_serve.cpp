@@ -18,6 +18,13 @@
 // and per-keyword counts are the histogram of each request's occurrences. If
 // a batch overflows its reservation (its occurrence count is still exact),
 // the batch runs once more with exactly that much room.
+//
+// Host copies are what a large request's latency is made of, so texts of
+// 1 MiB or more are copied at submit into pinned blocks from a pool and go to
+// the device from there (small ones are gathered in a per-worker pinned
+// staging buffer), and a batch of one request with 1 MiB or more of
+// occurrences leaves them in a pinned block the request keeps until it is
+// waited for.
 #include <cuda_runtime.h>
 
 #include <algorithm>
