@@ -331,12 +331,12 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             // one request with many occurrences: they (with text index 0 already)
             // and the batch's counts, which are the request's, land in a pinned
             // block the request keeps until it is waited for; no copy on the host
-            const bool handoff = d_cnt && mb >= kHandoffBytes;
             std::shared_ptr<PinnedPool::Block> blk;
+            if (d_cnt && mb >= kHandoffBytes) blk = pool.get(mb + (size_t)P * 8);  // none: the worker's buffer
+            const bool handoff = blk != nullptr;
             void* dst = nullptr;
             if (handoff) {
-                blk = pool.get(mb + (size_t)P * 8);
-                dst = blk ? blk->p : nullptr;
+                dst = blk->p;
             } else if (results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
                 dst = results.p;
             }
@@ -532,10 +532,9 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
         }
     }
     try {
-        if (nb >= kHandoffBytes) {
-            const uint64_t held = t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : nb;
-            r->text_block = s->pool.get(held);
-            if (!r->text_block) return AC_ERR_OOM;
+        const uint64_t held = t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : nb;
+        if (nb >= kHandoffBytes) r->text_block = s->pool.get(held);  // no pinned memory: staged instead
+        if (r->text_block) {
             std::memcpy(r->text_block->p, t->data, nb);
             std::memset((uint8_t*)r->text_block->p + nb, 'A', held - nb);
         } else {
