@@ -460,6 +460,22 @@ int ac_serve_submit(ac_server* srv, uint32_t slot, const ac_text* text, uint64_t
  * n_matches set when capacity is too small - in both cases the ticket stays
  * valid and the call can be repeated - or the request's own error. */
 int ac_serve_wait(ac_server* srv, uint64_t ticket, ac_result* result, int64_t timeout_us);
+/* A finished request's results, left where the server holds them. */
+typedef struct {
+    const ac_match* matches;  /* HOST, n_matches occurrences, text_id 0 */
+    uint64_t n_matches;
+    const uint64_t* counts;   /* HOST, n_counts per-keyword counts           */
+    uint64_t n_counts;
+    void* handle;             /* pass to ac_serve_release when done with both */
+} ac_served;
+/* Like ac_serve_wait, but without copying: on completion fills *out with
+ * the request's own occurrences and counts, forgets the ticket, and keeps
+ * that memory valid until ac_serve_release(out->handle) - also after
+ * ac_serve_destroy. Returns AC_ERR_TIMEOUT (ticket kept) or the request's
+ * own error (ticket forgotten, nothing to release). */
+int ac_serve_take(ac_server* srv, uint64_t ticket, ac_served* out, int64_t timeout_us);
+/* Gives back the memory of one ac_serve_take result (null: no-op). */
+void ac_serve_release(void* handle);
 int ac_serve_stats(ac_server* srv, ac_serve_stats_t* out);
 /* Finishes in-flight work, then frees everything. */
 void ac_serve_destroy(ac_server* srv);

@@ -435,6 +435,27 @@ def autotune(dfa: Dfa, packed_sample: torch.Tensor, n_bases: int, stream=None) -
 # ----------------------------------------------------------------- serving
 
 
+class _Taken:
+    """Owns one ac_serve_take result; gives it back when the last view goes."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if self.handle:
+            lib().ac_serve_release(self.handle)
+            self.handle = None
+
+
+def _view(addr, n: int, owner) -> np.ndarray:
+    """int64 numpy view of n values at addr, keeping owner alive while referenced."""
+    if n == 0 or not addr:
+        return np.zeros(n, dtype=np.int64)
+    buf = (ctypes.c_int64 * n).from_address(addr)
+    buf._owner = owner
+    return np.ctypeslib.as_array(buf)
+
+
 class Server:
     """Continuous-batching scan server (ac_serve_*)."""
 
@@ -476,13 +497,21 @@ class Server:
     def wait(self, ticket: int, slot: int, capacity: int | None = None, timeout_us: int = -1):
         """Returns (matches (k,2) int64 numpy [pos, pid], counts int64[P], n_matches).
 
-        capacity None: the exact count is asked for first (a wait with no room
-        reports it and keeps the ticket), so the occurrences are copied once,
-        into an array of exactly that size. An int: that much room is tried
-        first, and the exact size only on overflow; the array returned is then
-        the first n_matches rows of the one allocated. Served occurrences carry
-        text index 0, so column 1 is the keyword id as it stands."""
-        cap = 0 if capacity is None else int(capacity)
+        capacity None: nothing is copied (ac_serve_take). The two arrays are
+        views of the server's own copy of the results, which is given back
+        (ac_serve_release) once neither array is referenced any more. An int:
+        the results are copied (ac_serve_wait) into arrays of the caller's, that
+        much room first and the exact size on overflow; the matches returned
+        are then the first n_matches rows of the array allocated. Served
+        occurrences carry text index 0, so column 1 is the keyword id as it
+        stands."""
+        if capacity is None:
+            out = N.Served()
+            N.check(lib().ac_serve_take(self.h, ticket, ctypes.byref(out), timeout_us), "ac_serve_take")
+            held = _Taken(out.handle)
+            k, pc = int(out.n_matches), int(out.n_counts)
+            return _view(out.matches, 2 * k, held).reshape(k, 2), _view(out.counts, pc, held), k
+        cap = int(capacity)
         for _ in range(2):
             raw = np.empty((max(cap, 1), 2), dtype=np.int64)
             cnt = np.empty(self._npat[slot], dtype=np.int64)

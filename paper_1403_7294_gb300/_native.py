@@ -96,6 +96,10 @@ class ServeOpts(ctypes.Structure):
     ]
 
 
+class Served(ctypes.Structure):
+    _fields_ = [("matches", P), ("n_matches", u64), ("counts", P), ("n_counts", u64), ("handle", P)]
+
+
 class ServeStats(ctypes.Structure):
     _fields_ = [
         ("submitted", u64), ("completed", u64), ("rejected", u64), ("failed", u64),
@@ -139,6 +143,8 @@ SIGNATURES = {
     "ac_serve_add_dfa": (ctypes.c_int, [P, P, ctypes.POINTER(u32)]),
     "ac_serve_submit": (ctypes.c_int, [P, u32, ctypes.POINTER(Text), ctypes.POINTER(u64)]),
     "ac_serve_wait": (ctypes.c_int, [P, u64, ctypes.POINTER(Result), i64]),
+    "ac_serve_take": (ctypes.c_int, [P, u64, ctypes.POINTER(Served), i64]),
+    "ac_serve_release": (None, [P]),
     "ac_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ServeStats)]),
     "ac_serve_destroy": (None, [P]),
 }

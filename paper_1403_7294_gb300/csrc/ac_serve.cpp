@@ -49,12 +49,12 @@ using Clock = std::chrono::steady_clock;
 // Pinned host blocks reused across requests: a block stays with the request
 // whose text or results it holds until the request is forgotten, then goes
 // back to the free list (beyond kKeepFree free bytes it is released).
-class PinnedPool {
+class PinnedPool : public std::enable_shared_from_this<PinnedPool> {
   public:
-    struct Block {
+    struct Block {  // keeps its pool alive: a taken result may outlive the server
         void* p = nullptr;
         size_t cap = 0;
-        PinnedPool* pool = nullptr;
+        std::shared_ptr<PinnedPool> pool;
         ~Block() { pool->put(p, cap); }
     };
     ~PinnedPool() {
@@ -78,7 +78,7 @@ class PinnedPool {
         auto b = std::make_shared<Block>();
         b->p = p;
         b->cap = cap;
-        b->pool = this;
+        b->pool = shared_from_this();
         return b;
     }
 
@@ -180,7 +180,7 @@ struct PinnedBuf {
 }  // namespace
 
 struct ac_server {
-    PinnedPool pool;  // result blocks of one-request batches (destroyed last)
+    std::shared_ptr<PinnedPool> pool = std::make_shared<PinnedPool>();  // pinned text and result blocks
     ac_serve_opts opts{};
     int device = 0;
     std::mutex mu;
@@ -332,7 +332,7 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             // and the batch's counts, which are the request's, land in a pinned
             // block the request keeps until it is waited for; no copy on the host
             std::shared_ptr<PinnedPool::Block> blk;
-            if (d_cnt && mb >= kHandoffBytes) blk = pool.get(mb + (size_t)P * 8);  // none: the worker's buffer
+            if (d_cnt && mb >= kHandoffBytes) blk = pool->get(mb + (size_t)P * 8);  // none: the worker's buffer
             const bool handoff = blk != nullptr;
             void* dst = nullptr;
             if (handoff) {
@@ -533,7 +533,7 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
     }
     try {
         const uint64_t held = t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : nb;
-        if (nb >= kHandoffBytes) r->text_block = s->pool.get(held);  // no pinned memory: staged instead
+        if (nb >= kHandoffBytes) r->text_block = s->pool->get(held);  // no pinned memory: staged instead
         if (r->text_block) {
             std::memcpy(r->text_block->p, t->data, nb);
             std::memset((uint8_t*)r->text_block->p + nb, 'A', held - nb);
@@ -581,6 +581,42 @@ extern "C" int ac_serve_wait(ac_server* s, uint64_t ticket, ac_result* res, int6
     if (res->counts && r->n_counts) std::memcpy(res->counts, r->count_data(), r->n_counts * 8);
     return AC_OK;
 }
+
+namespace {
+struct Taken {  // what an ac_serve_take handle owns
+    std::shared_ptr<Request> r;
+};
+}  // namespace
+
+extern "C" int ac_serve_take(ac_server* s, uint64_t ticket, ac_served* out, int64_t timeout_us) {
+    if (!s || !out) return AC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof *out);
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->by_ticket.find(ticket);
+        if (it == s->by_ticket.end()) return AC_ERR_NOT_FOUND;
+        r = it->second;
+        auto ready = [&] { return r->done; };
+        if (timeout_us < 0) {
+            s->cv_done.wait(lk, ready);
+        } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+            return AC_ERR_TIMEOUT;
+        }
+        s->by_ticket.erase(ticket);
+    }
+    if (r->status != AC_OK) return r->status;
+    Taken* t = new (std::nothrow) Taken{r};
+    if (!t) return AC_ERR_OOM;
+    out->matches = r->match_data();
+    out->n_matches = r->n_matches;
+    out->counts = r->count_data();
+    out->n_counts = r->n_counts;
+    out->handle = t;
+    return AC_OK;
+}
+
+extern "C" void ac_serve_release(void* handle) { delete static_cast<Taken*>(handle); }
 
 extern "C" int ac_serve_stats(ac_server* s, ac_serve_stats_t* o) {
     if (!s || !o) return AC_ERR_INVALID_ARG;

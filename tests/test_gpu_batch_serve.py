@@ -222,13 +222,19 @@ def test_serve_large_results_handed_over():
         assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:])
         assert np.array_equal(c, counts)
     again = srv.submit(slot, texts[0])  # a block back from the pool
-    m, c, k = srv.wait(again, slot)
+    m, c, k = srv.wait(again, slot)  # views of the server's copy, no copy made
     want, counts = oracle_canonical(pats, texts[0])
     assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and np.array_equal(c, counts)
+    with pytest.raises(acg.AcError) as e:
+        srv.wait(again, slot)  # taken: the ticket is gone
+    assert e.value.status == N.AC_ERR_NOT_FOUND
     srv.submit(slot, texts[1])  # left unclaimed: its block goes back when the server closes
     st = srv.stats()
     srv.close()
     assert st["failed"] == 0
+    # a taken result stays valid after the server is gone; its block is given back with the arrays
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and np.array_equal(c, counts)
+    del m, c
 
 
 @pytest.mark.parametrize("form", ["ascii", "packed"])
