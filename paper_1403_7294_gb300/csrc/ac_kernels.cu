@@ -809,17 +809,77 @@ __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t ho
     if (qn) drain(q, qn, &em);
 }
 
+// One word of 16 ASCII bases (the bytes of q.x, q.y, q.z, q.w in order):
+// base j's 2-bit code at bits 2j, and in ok whether all 16 bytes are A, C, G
+// or T (either case when fold). Four bytes at a time: ((x >> 1) ^ (x >> 2)) & 3
+// in every byte is the code (A, C, G, T -> 0, 1, 2, 3 in either case; bits
+// shifted across bytes land above bit 1 and are masked off). The letter each
+// code stands for is put back with one byte permute of "ACGT" selected by the
+// four codes; a byte is a base exactly when it equals that letter (after the
+// case fold). The multiply by 0x01041040 moves the code of byte k to bit
+// 24 + 2k while every cross product lands below bit 24 in its own two-bit
+// field, so the top byte is the four codes in order.
+__device__ __forceinline__ uint32_t pack16(const uint4 q, bool fold, bool& ok) {
+    const uint32_t by[4] = {q.x, q.y, q.z, q.w};
+    uint32_t word = 0, diff = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t x = by[k];
+        const uint32_t c = ((x >> 1) ^ (x >> 2)) & 0x03030303u;
+        const uint32_t t = c | (c >> 4);                            // bytes 0 and 2: two codes a nibble
+        const uint32_t sel = (t & 0xffu) | ((t >> 8) & 0xff00u);    // the four codes, one per nibble
+        diff |= (fold ? (x & 0xdfdfdfdfu) : x) ^ __byte_perm(0x54474341u, 0u, sel);  // "ACGT"
+        word |= ((c * 0x01041040u) >> 24) << (8 * k);
+    }
+    ok = diff == 0;
+    return word;
+}
+
+// Index (0-15) of the first byte of q that is not A, C, G or T.
+__device__ __noinline__ uint32_t first_bad16(const uint4 q, bool fold) {
+    const uint32_t by[4] = {q.x, q.y, q.z, q.w};
+    for (uint32_t i = 0; i < 16; ++i) {
+        const uint32_t c = (by[i >> 2] >> (8 * (i & 3))) & 0xffu;
+        const uint32_t u = fold ? (c & 0xdfu) : c;
+        if (!((u == 'A') | (u == 'C') | (u == 'G') | (u == 'T'))) return i;
+    }
+    return 16;
+}
+
+// ASCII bases to 2-bit words (16 bases a word, base j at bits 2j); *bad gets
+// the smallest offset of a byte that is not a base (either case when fold).
 __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint32_t* __restrict__ packed, int fold,
                             unsigned long long* bad) {
     const uint64_t nw = (n + 15) >> 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += stride) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t first_bad = ~0ull;
+    // a warp takes 128 whole words (2,048 bases) at a time: load j of lane t is
+    // word 32j + t, so each load covers 512 contiguous bytes and each store 128
+    const uint64_t lane = threadIdx.x & 31;
+    const uint64_t warp = t0 >> 5, n_warps = stride >> 5;
+    const uint64_t ng = ((reinterpret_cast<uintptr_t>(ascii) & 15) == 0) ? (n >> 11) : 0;
+    for (uint64_t g = warp; g < ng; g += n_warps) {
+        const uint4* src = reinterpret_cast<const uint4*>(ascii) + 128 * g + lane;
+        uint4 q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = __ldcs(src + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            bool ok;
+            const uint64_t w = 128 * g + 32 * j + lane;
+            packed[w] = pack16(q[j], fold != 0, ok);
+            if (!ok) first_bad = min(first_bad, 16 * w + first_bad16(q[j], fold != 0));
+        }
+    }
+    // the rest one word at a time: texts not 16-byte aligned, and the last bases
+    for (uint64_t w = 128 * ng + t0; w < nw; w += stride) {
         const uint64_t b0 = w << 4;
-        uint32_t by[4];
+        uint4 q;
         if (b0 + 16 <= n && ((reinterpret_cast<uintptr_t>(ascii + b0) & 15) == 0)) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(ascii + b0));
-            by[0] = v.x; by[1] = v.y; by[2] = v.z; by[3] = v.w;
-        } else {
+            q = __ldcs(reinterpret_cast<const uint4*>(ascii + b0));
+        } else {  // past the end: 'A' (code 0, valid)
+            uint32_t by[4];
             for (int k = 0; k < 4; ++k) {
                 uint32_t x = 0;
                 for (int i = 0; i < 4; ++i) {
@@ -828,20 +888,13 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint3
                 }
                 by[k] = x;
             }
+            q = make_uint4(by[0], by[1], by[2], by[3]);
         }
-        uint32_t word = 0;
-        uint64_t first_bad = ~0ull;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            uint32_t c = (by[i >> 2] >> (8 * (i & 3))) & 0xffu;
-            const uint32_t u = fold ? (c & 0xdfu) : c;
-            const bool ok = (u == 'A') | (u == 'C') | (u == 'G') | (u == 'T');
-            if (!ok && b0 + i < n && first_bad == ~0ull) first_bad = b0 + i;
-            word |= (((c >> 1) ^ (c >> 2)) & 3u) << (2 * i);  // A,C,G,T (either case) -> 0,1,2,3
-        }
-        packed[w] = word;
-        if (first_bad != ~0ull) atomicMin(bad, (unsigned long long)first_bad);
+        bool ok;
+        packed[w] = pack16(q, fold != 0, ok);
+        if (!ok) first_bad = min(first_bad, b0 + first_bad16(q, fold != 0));
     }
+    if (first_bad != ~0ull) atomicMin(bad, (unsigned long long)first_bad);
 }
 
 // Copies n bases of a packed text from base src_off of src to base dst_off
@@ -1086,9 +1139,17 @@ int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold
     if (n == 0) return 0;
     const uint64_t nw = (n + 15) >> 4;
     const DeviceProps& p = ac_device_props();
-    uint64_t blocks = (nw + 255) / 256;
-    const uint64_t cap = (uint64_t)p.sms * 8;
+    // one wave of resident blocks (each strides over the text), no more
+    static std::atomic<int> resident{0};
+    if (resident.load() == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pack_kernel, 256, 0) != cudaSuccess || nb < 1) nb = 1;
+        resident.store(nb);
+    }
+    uint64_t blocks = (nw + 4 * 256 - 1) / (4 * 256);  // four words a thread per pass
+    const uint64_t cap = (uint64_t)p.sms * (uint64_t)resident.load();
     if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
     pack_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ascii, n, packed, fold ? 1 : 0, bad);
     return (int)cudaGetLastError();
 }

@@ -33,17 +33,37 @@ def to_dev(b: bytes) -> torch.Tensor:
 
 
 def test_pack_round_trip_and_alphabet():
+    """Packing is the definition (A, C, G, T -> 0, 1, 2, 3, base j at bits 2j) for 16-byte
+    aligned texts (64 bases at a time, then word by word) and texts at every misalignment;
+    case folding; and the reported offset is the first byte that is not a base."""
     rng = random.Random(1)
-    for n in (1, 15, 16, 17, 63, 64, 65, 1000, 4097):
-        txt = rand_dna(rng, n)
-        packed = acg.pack(to_dev(txt))
-        codes = unpack_codes(packed, n).cpu().numpy()
-        assert codes.tolist() == [b"ACGT".index(c) for c in txt]
+    base = to_dev(rand_dna(rng, 300_000))
+    for n in (1, 15, 16, 17, 63, 64, 65, 127, 128, 129, 1000, 4097, 100_003):
+        for shift in (0, 1, 4, 15):  # data_ptr offset: 0 keeps the 16-byte alignment
+            t = base[shift : shift + n]
+            packed = acg.pack(t)
+            codes = unpack_codes(packed, n).cpu().numpy()
+            assert codes.tolist() == [b"ACGT".index(c) for c in bytes(t.cpu().numpy())], (n, shift)
     low = to_dev(b"acgtACGT")
     assert unpack_codes(acg.pack(low, fold_case=True), 8).tolist() == [0, 1, 2, 3, 0, 1, 2, 3]
+    mixed = bytes(rng.choice(b"ACGTacgt") for _ in range(1000))
+    assert unpack_codes(acg.pack(to_dev(mixed), fold_case=True), 1000).tolist() == [
+        b"ACGT".index(bytes([c]).upper()) for c in mixed]
     with pytest.raises(acg.AcError) as e:
         acg.pack(to_dev(b"ACGTNACGT"))
     assert e.value.status == N.AC_ERR_ALPHABET and "offset 4" in str(e.value)
+    for n, where, fold in ((1000, [5, 700], False), (1000, [64, 63 + 64], False), (4096, [4095], False),
+                           (100_003, [99_999, 100_002], False), (1000, [333], True), (200, [0, 199], False)):
+        t = bytearray(rand_dna(rng, n))
+        if fold:
+            t = bytearray(bytes(t).lower())
+        for k, i in enumerate(where):
+            t[i] = (b"Nn" if fold else b"NaU")[k % (2 if fold else 3)]
+        for shift in (0, 3):
+            dev = to_dev(b"A" * shift + bytes(t))[shift:]
+            with pytest.raises(acg.AcError) as e:
+                acg.pack(dev, fold_case=fold)
+            assert e.value.status == N.AC_ERR_ALPHABET and f"offset {min(where)}" in str(e.value), (n, where, shift)
 
 
 def test_worked_example_dna():
