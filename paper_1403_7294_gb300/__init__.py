@@ -442,9 +442,12 @@ class _Taken:
         self.handle = handle
 
     def __del__(self):
-        if self.handle:
-            lib().ac_serve_release(self.handle)
-            self.handle = None
+        h, self.handle = self.handle, None
+        if h:
+            try:
+                lib().ac_serve_release(h)
+            except Exception:  # interpreter shutdown: the process gives the memory back
+                pass
 
 
 def _view(addr, n: int, owner) -> np.ndarray:
