@@ -65,6 +65,11 @@ def test_host_packed_equals_device(work):
     _same(acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=N_BASES), want)
 
 
+def test_host_two_blocks_per_sm_shape(work):
+    pats, d, dev, host, want = work
+    _same(acg.scan(d, host, stride=3, threads=640), want)
+
+
 def test_one_shot_host_path_agrees(work):
     pats, d, dev, host, want = work
     _same(acg.scan(d, host, stats=True), want)

@@ -34,8 +34,8 @@ def _pieces(rng, n, lmax):
 
 
 @pytest.mark.parametrize("form", ["ascii_dev", "ascii_host", "packed_dev", "packed_host"])
-@pytest.mark.parametrize("stride", [1, 2, 3])
-def test_stream_equals_one_scan(form, stride):
+@pytest.mark.parametrize("stride,threads", [(1, 0), (2, 0), (3, 0), (3, 640)])
+def test_stream_equals_one_scan(form, stride, threads):
     text, pats, rng = _text_and_patterns(31, 60_000)
     d = acg.build(pats)
     lmax = max(len(p) for p in pats)
@@ -52,7 +52,7 @@ def test_stream_equals_one_scan(form, stride):
             packed = acg.pack(torch.tensor(list(piece), dtype=torch.uint8, device="cuda"))
             arg = packed if form == "packed_dev" else packed.cpu().numpy()
             kw = {"encoding": N.AC_TEXT_PACKED2, "n_bases": b - a}
-        r = s.scan(arg, capacity=2, stride=stride, **kw)  # tiny capacity: the stream retries the same piece
+        r = s.scan(arg, capacity=2, stride=stride, threads=threads, **kw)  # tiny capacity: the stream retries the piece
         rows.append(r.canonical())
         csum += r.counts.cpu().numpy()
     got = np.concatenate(rows)
