@@ -858,22 +858,57 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint3
     // word 32j + t, so each load covers 512 contiguous bytes and each store 128
     const uint64_t lane = threadIdx.x & 31;
     const uint64_t warp = t0 >> 5, n_warps = stride >> 5;
-    const uint64_t ng = ((reinterpret_cast<uintptr_t>(ascii) & 15) == 0) ? (n >> 11) : 0;
-    for (uint64_t g = warp; g < ng; g += n_warps) {
-        const uint4* src = reinterpret_cast<const uint4*>(ascii) + 128 * g + lane;
-        uint4 q[4];
+    const uint32_t off = (uint32_t)(reinterpret_cast<uintptr_t>(ascii) & 15);
+    uint64_t v0 = 0, vn = 0;  // words [v0, v0 + vn) go 128 per warp pass
+    if (off == 0) {
+        vn = 128 * (n >> 11);
+        for (uint64_t g = warp; 128 * g < vn; g += n_warps) {
+            const uint4* src = reinterpret_cast<const uint4*>(ascii) + 128 * g + lane;
+            uint4 q[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = __ldcs(src + 32 * j);
+            for (int j = 0; j < 4; ++j) q[j] = __ldcs(src + 32 * j);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            bool ok;
-            const uint64_t w = 128 * g + 32 * j + lane;
-            packed[w] = pack16(q[j], fold != 0, ok);
-            if (!ok) first_bad = min(first_bad, 16 * w + first_bad16(q[j], fold != 0));
+            for (int j = 0; j < 4; ++j) {
+                bool ok;
+                const uint64_t w = 128 * g + 32 * j + lane;
+                packed[w] = pack16(q[j], fold != 0, ok);
+                if (!ok) first_bad = min(first_bad, 16 * w + first_bad16(q[j], fold != 0));
+            }
+        }
+    } else {
+        // counted from the aligned address below the text, chunk m holds text bytes
+        // [16m - off, 16m - off + 16), so word w is bytes off.. of chunk w and the
+        // rest of chunk w + 1. Words from 1 on read no byte before the text, and up
+        // to word (n + off - 32) / 16 none after it.
+        const uint4* base = reinterpret_cast<const uint4*>(ascii - off);
+        const uint64_t last = (n + off >= 32) ? (n + off - 32) >> 4 : 0;
+        v0 = 1;
+        vn = 128 * (last >> 7);
+        const uint32_t r = off >> 2, sh = 8 * (off & 3);
+        for (uint64_t g = warp; 128 * g < vn; g += n_warps) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t w = 1 + 128 * g + 32 * j + lane;
+                const uint4 a = __ldcs(base + w), b = __ldcs(base + w + 1);
+                uint4 q;  // the 16 bytes from byte off of a:b (r whole words, then sh bits)
+                switch (r) {  // the same for every thread
+                    case 0: q = make_uint4(__funnelshift_r(a.x, a.y, sh), __funnelshift_r(a.y, a.z, sh),
+                                           __funnelshift_r(a.z, a.w, sh), __funnelshift_r(a.w, b.x, sh)); break;
+                    case 1: q = make_uint4(__funnelshift_r(a.y, a.z, sh), __funnelshift_r(a.z, a.w, sh),
+                                           __funnelshift_r(a.w, b.x, sh), __funnelshift_r(b.x, b.y, sh)); break;
+                    case 2: q = make_uint4(__funnelshift_r(a.z, a.w, sh), __funnelshift_r(a.w, b.x, sh),
+                                           __funnelshift_r(b.x, b.y, sh), __funnelshift_r(b.y, b.z, sh)); break;
+                    default: q = make_uint4(__funnelshift_r(a.w, b.x, sh), __funnelshift_r(b.x, b.y, sh),
+                                            __funnelshift_r(b.y, b.z, sh), __funnelshift_r(b.z, b.w, sh)); break;
+                }
+                bool ok;
+                packed[w] = pack16(q, fold != 0, ok);
+                if (!ok) first_bad = min(first_bad, 16 * w + first_bad16(q, fold != 0));
+            }
         }
     }
-    // the rest one word at a time: texts not 16-byte aligned, and the last bases
-    for (uint64_t w = 128 * ng + t0; w < nw; w += stride) {
+    // the rest one word at a time (word 0 of a text that is not 16-byte aligned, and the last bases)
+    auto one_word = [&](uint64_t w) {
         const uint64_t b0 = w << 4;
         uint4 q;
         if (b0 + 16 <= n && ((reinterpret_cast<uintptr_t>(ascii + b0) & 15) == 0)) {
@@ -893,7 +928,9 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint3
         bool ok;
         packed[w] = pack16(q, fold != 0, ok);
         if (!ok) first_bad = min(first_bad, b0 + first_bad16(q, fold != 0));
-    }
+    };
+    if (vn && v0 == 1 && t0 == 0) one_word(0);
+    for (uint64_t w = (vn ? v0 + vn : 0) + t0; w < nw; w += stride) one_word(w);
     if (first_bad != ~0ull) atomicMin(bad, (unsigned long long)first_bad);
 }
 
