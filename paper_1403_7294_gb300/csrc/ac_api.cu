@@ -95,6 +95,27 @@ unsigned long long* pinned_pad() {
     return pad;
 }
 
+// Sets a 4-word counter block to {0, 0, ~0, ~0} (occurrences, cursor, bad
+// offset, pad) with one copy from a constant pinned block.
+cudaError_t init_counters(unsigned long long* d_ctr, cudaStream_t st) {
+    static unsigned long long* init = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        if (cudaMallocHost(&p, 4 * sizeof(unsigned long long)) == cudaSuccess) {
+            unsigned long long* v = static_cast<unsigned long long*>(p);
+            v[0] = v[1] = 0;
+            v[2] = v[3] = ~0ull;
+            init = v;
+        }
+    });
+    if (!init) {  // no pinned memory: two memsets
+        cudaError_t e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st);
+        return e != cudaSuccess ? e : cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st);
+    }
+    return cudaMemcpyAsync(d_ctr, init, 4 * sizeof(unsigned long long), cudaMemcpyHostToDevice, st);
+}
+
 struct Events {
     bool on = false;
     cudaEvent_t ev[8] = {};
@@ -346,13 +367,23 @@ int finish(cudaStream_t st, const unsigned long long* d_counter, const unsigned 
            ac_result* r, const ac_match* d_matches, const unsigned long long* d_counts, uint32_t n_pat) {
     unsigned long long* pad = pinned_pad();
     if (!pad) return AC_ERR_OOM;
-    cudaError_t e = cudaMemcpyAsync(pad, d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && d_bad)
-        e = cudaMemcpyAsync(pad + 1, d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_status(e);
-    const uint64_t nm = pad[0];
-    const uint64_t bad = d_bad ? pad[1] : ~0ull;
+    cudaError_t e;
+    uint64_t nm = 0, bad = ~0ull;
+    if (d_bad == d_counter + 2) {  // counter and bad offset of one block: one read
+        e = cudaMemcpyAsync(pad, d_counter, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        nm = pad[0];
+        bad = pad[2];
+    } else {
+        e = cudaMemcpyAsync(pad, d_counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && d_bad)
+            e = cudaMemcpyAsync(pad + 1, d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        nm = pad[0];
+        bad = d_bad ? pad[1] : ~0ull;
+    }
     r->n_matches = nm;
     r->bad_offset = bad;
     if (bad != ~0ull) return AC_ERR_ALPHABET;
@@ -562,9 +593,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     unsigned long long* d_hits = nullptr;
     if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
     if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
     ev.rec(1);
     if (text->encoding == AC_TEXT_ASCII && n) {
@@ -642,8 +671,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
     if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
     if ((e = sc.get((void**)&d_m, r->capacity * sizeof(ac_match))) != cudaSuccess) return cuda_status(e);
     if (r->counts && (e = sc.get((void**)&d_counts, (size_t)h.n_patterns * 8)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 16, st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 16, st)) != cudaSuccess) return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
     cudaEvent_t ready, in_done[kPipeMaxPieces], cnt_done[kPipeMaxPieces], out_done;
     cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
@@ -819,9 +847,7 @@ extern "C" int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_re
     unsigned long long* d_hits = nullptr;
     if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
     if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
     ev.rec(1);
     const uint32_t* words = nullptr;
@@ -907,9 +933,7 @@ extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, 
     unsigned long long* d_hits = nullptr;
     if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
     if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
     ev.rec(1);
     const uint32_t* pw = nullptr;
@@ -1064,9 +1088,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
         return cuda_status(e);
     if ((e = sc.get((void**)&d_parts, std::max<size_t>(k, 1) * sizeof(PartDesc))) != cudaSuccess)
         return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, set->total_states * 8, st)) != cudaSuccess) return cuda_status(e);
     std::vector<PartDesc> pd(k);
     uint64_t off = 0;
@@ -1216,9 +1238,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     unsigned long long* d_hits = nullptr;
     if ((e = sc.get((void**)&d_ctr, 4 * sizeof(unsigned long long))) != cudaSuccess) return cuda_status(e);
     if ((e = sc.get((void**)&d_hits, (size_t)h.n_states * 8)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(d_ctr + 2, 0xff, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-        return cuda_status(e);
+    if ((e = init_counters(d_ctr, st)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(d_hits, 0, (size_t)h.n_states * 8, st)) != cudaSuccess) return cuda_status(e);
 
     // ---- every text onto the device, packed, each starting on a 64-base boundary
