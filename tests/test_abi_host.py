@@ -345,3 +345,37 @@ def test_breadth_first_numbering():
     rng = random.Random(3)
     t = acg.build(rand_set(rng, 200, 5, 12), host_only=True).tables()
     assert np.all(np.diff(t["depth"].astype(np.int64)) >= 0)  # depth non-decreasing in id order
+
+
+def test_taken_result_views_release_once_when_the_last_view_dies(monkeypatch):
+    """Server.wait without a capacity returns numpy views of the server's own copy
+    (ac_serve_take); the copy is given back (ac_serve_release) exactly once, when neither
+    the occurrence view nor the count view is referenced any more."""
+    import ctypes
+    import gc
+
+    import numpy as np
+
+    released = []
+
+    class FakeLib:
+        def ac_serve_release(self, h):
+            released.append(h)
+
+    monkeypatch.setattr(acg, "lib", lambda: FakeLib())
+    occ = (ctypes.c_int64 * 6)(10, 1, 20, 2, 30, 3)
+    cnt = (ctypes.c_int64 * 4)(0, 1, 1, 1)
+    held = acg._Taken(12345)
+    m = acg._view(ctypes.addressof(occ), 6, held).reshape(3, 2)
+    c = acg._view(ctypes.addressof(cnt), 4, held)
+    del held
+    gc.collect()
+    assert m.tolist() == [[10, 1], [20, 2], [30, 3]] and c.tolist() == [0, 1, 1, 1]
+    assert released == []
+    del m
+    gc.collect()
+    assert released == [] and c.sum() == 3
+    del c
+    gc.collect()
+    assert released == [12345]
+    assert acg._view(0, 0, None).shape == (0,)
