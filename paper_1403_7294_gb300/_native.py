@@ -159,7 +159,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         return _LIB
     if not os.path.exists(path):
         raise ImportError(
-            f"libac.so not found at {path}: build it first (python -m paper_1403_7294_gb300.build); "
+            f"libac.so not found at {path}: build it first (python -m paper_1403_7294_gb300._compile); "
             "there is no CPU fallback"
         )
     lib = ctypes.CDLL(path)

@@ -379,3 +379,14 @@ def test_taken_result_views_release_once_when_the_last_view_dies(monkeypatch):
     gc.collect()
     assert released == [12345]
     assert acg._view(0, 0, None).shape == (0,)
+
+
+def test_build_entry_leaves_the_public_build_function():
+    """The in-tree compile step lives in a module whose import cannot shadow acg.build:
+    building and then building a machine works in one process."""
+    import __graft_entry__
+
+    __graft_entry__.build()  # nothing to do when the library is current
+    assert callable(acg.build)
+    d = acg.build([b"ACGT", b"CG"], host_only=True)
+    assert d.info["n_states"] == 7  # root, A, AC, ACG, ACGT, C, CG
