@@ -58,6 +58,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(N.Result) == 48
     assert ctypes.sizeof(N.ScanOpts) == 48
     assert ctypes.sizeof(N.ScanStats) == 56
+    assert ctypes.sizeof(N.Served) == 40  # ac_served: two pointers, two counts, a handle
 
 
 # ------------------------------------------------------------ validation
