@@ -85,9 +85,10 @@ typedef struct {
     uint32_t stride2_states; /* rows of the two-base table: the first (breadth-first, i.e.
                                 shallowest) this many states; 0 = every state, up to 2^24.
                                 Steps from deeper states take two one-base lookups.       */
-    uint32_t stride3_states; /* rows of the three-base table, likewise; 0 = min(S, 2^17);
-                                at most 2^22. Three-base steps from deeper states take a
-                                two-base and a one-base lookup (or three one-base ones).  */
+    uint32_t stride3_states; /* rows of the three-base table, likewise; 0 = min(S, 2^21)
+                                (every state of machines up to 2^21 states); at most 2^22.
+                                Three-base steps from deeper states take a two-base or a
+                                one-base lookup instead.                                  */
 } ac_build_opts;
 
 /*
@@ -304,7 +305,8 @@ int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_
  *
  * Same semantics as ac_scan, restricted to device-resident inputs/outputs:
  * text must be AC_TEXT_PACKED2 with on_device = 1; result->on_device must be
- * 1 (matches and counts in device memory). opts (nullable) as for ac_scan.
+ * 1 (matches and counts in device memory). opts (nullable) as for ac_scan,
+ * with the same checks: stride 2 or 3 needs the two- or three-base table.
  * Synchronises `stream` once to learn n_matches.
  *
  * The first call on a device looks up the device address of the scratch
@@ -479,6 +481,42 @@ void ac_serve_release(void* handle);
 int ac_serve_stats(ac_server* srv, ac_serve_stats_t* out);
 /* Finishes in-flight work, then frees everything. */
 void ac_serve_destroy(ac_server* srv);
+
+/* ------------------------------------------ fault injection and accounting
+ * The paper has no counterpart to these two calls; they serve failure
+ * testing and leak checks. Fault injection stays on the host: no injected
+ * failure reaches the GPU.
+ *
+ * ac_fault_inject sets the process-wide fault plan, replacing any earlier
+ * plan (and the AC_FAULT environment variable, which is read once, at the
+ * library's first allocation, when no plan was set). spec is a
+ * comma-separated list of
+ *   "oom@k"       the k-th device allocation (k >= 1) of the library from now
+ *                 on fails as if the device were full: the call that made it
+ *                 returns AC_ERR_OOM (a serving request, its own error);
+ *   "cuda_err@k"  the k-th kernel launch of the library from now on is not
+ *                 made and reports a launch failure: the call returns
+ *                 AC_ERR_CUDA.
+ * NULL or "" clears the plan. Counting restarts at every call. Every call
+ * that fails this way releases what it allocated (see ac_mem_usage).
+ * Errors: AC_ERR_INVALID_ARG for a spec it cannot parse (the plan is kept).
+ */
+int ac_fault_inject(const char* spec);
+
+typedef struct {
+    uint64_t pool_used_bytes;     /* stream-ordered pool memory in use on the current device
+                                     (per-call scratch of the library; also any other user of
+                                     the device's default pool)                              */
+    uint64_t pool_reserved_bytes; /* memory the device's default pool holds                  */
+    uint64_t live_bytes;          /* device bytes held by the library's objects (dfa tables,
+                                     streams, batch plans) on all devices                    */
+    uint64_t live_allocations;    /* number of those allocations                             */
+    uint64_t allocations_seen;    /* device allocations counted since the fault plan was set */
+    uint64_t launches_seen;       /* kernel launches counted since the fault plan was set    */
+} ac_mem_usage_t;
+
+/* Fills *out (see ac_mem_usage_t). Errors: AC_ERR_INVALID_ARG, AC_ERR_CUDA. */
+int ac_mem_usage(ac_mem_usage_t* out);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,7 @@ from ._native import AcError
 
 __all__ = [
     "Dfa", "ScanResult", "build", "pack", "scan", "scan_failureless", "scan_batch", "BatchPlan", "Stream", "PartSet",
-    "build_partitioned", "autotune", "Server",
+    "build_partitioned", "autotune", "Server", "fault_inject", "mem_usage",
     "AcError", "lib",
 ]
 
@@ -430,6 +430,19 @@ def autotune(dfa: Dfa, packed_sample: torch.Tensor, n_bases: int, stream=None) -
     o = N.ScanOpts()
     N.check(lib().ac_autotune(dfa.h, ctypes.byref(desc), ctypes.byref(o), _stream_ptr(stream)), "ac_autotune")
     return {"threads": o.threads, "interleave": o.interleave, "hot_states": o.hot_states, "stride": o.stride}
+
+
+def fault_inject(spec: str | None) -> None:
+    """Sets the host-side fault plan (ac_fault_inject): "oom@k", "cuda_err@k", both comma-separated, or
+    None to clear it."""
+    N.check(lib().ac_fault_inject(spec.encode() if spec else None), "ac_fault_inject")
+
+
+def mem_usage() -> dict:
+    """Device memory the library holds (ac_mem_usage)."""
+    m = N.MemUsage()
+    N.check(lib().ac_mem_usage(ctypes.byref(m)), "ac_mem_usage")
+    return {k: getattr(m, k) for k, _ in N.MemUsage._fields_}
 
 
 # ----------------------------------------------------------------- serving

@@ -109,6 +109,13 @@ class ServeStats(ctypes.Structure):
     ]
 
 
+class MemUsage(ctypes.Structure):
+    _fields_ = [
+        ("pool_used_bytes", u64), ("pool_reserved_bytes", u64), ("live_bytes", u64), ("live_allocations", u64),
+        ("allocations_seen", u64), ("launches_seen", u64),
+    ]
+
+
 # name -> (restype, argtypes); every function declared in include/ac.h
 SIGNATURES = {
     "ac_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -147,6 +154,8 @@ SIGNATURES = {
     "ac_serve_release": (None, [P]),
     "ac_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ServeStats)]),
     "ac_serve_destroy": (None, [P]),
+    "ac_fault_inject": (ctypes.c_int, [ctypes.c_char_p]),
+    "ac_mem_usage": (ctypes.c_int, [ctypes.POINTER(MemUsage)]),
 }
 
 _LIB: ctypes.CDLL | None = None

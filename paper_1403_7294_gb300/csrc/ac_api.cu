@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "ac_internal.h"
@@ -27,36 +28,150 @@ int cuda_status(cudaError_t e) {
     return AC_ERR_CUDA;
 }
 
-// ---- host-side fault injection: AC_FAULT=oom@k makes the k-th device
-// allocation of the process (1-based) fail as if the device were full.
+// ---- host-side fault injection (ac_fault_inject, or AC_FAULT at the first
+// allocation): "oom@k" makes the k-th device allocation after the plan was
+// set fail as if the device were full; "cuda_err@k" makes the k-th kernel
+// launch report a launch failure without launching anything. Both are
+// counted from the moment the plan is set; nothing reaches the GPU.
 std::mutex g_fault_mu;
-long g_alloc_count = 0;
-long g_fault_oom_at = -2;
+bool g_fault_env_read = false;
+long g_alloc_count = 0, g_launch_count = 0;
+long g_fault_oom_at = -1, g_fault_launch_at = -1;
+
+bool parse_fault_plan(const char* spec, long* oom_at, long* launch_at) {
+    *oom_at = *launch_at = -1;
+    if (!spec || !*spec) return true;
+    const char* p = spec;
+    while (*p) {
+        long* slot = nullptr;
+        if (std::strncmp(p, "oom@", 4) == 0) {
+            slot = oom_at;
+            p += 4;
+        } else if (std::strncmp(p, "cuda_err@", 9) == 0) {
+            slot = launch_at;
+            p += 9;
+        } else {
+            return false;
+        }
+        char* end = nullptr;
+        const long k = std::strtol(p, &end, 10);
+        if (end == p || k < 1) return false;
+        *slot = k;
+        p = end;
+        if (*p == ',') {
+            if (!*++p) return false;  // a list does not end in a comma
+        } else if (*p) {
+            return false;
+        }
+    }
+    return true;
+}
+
+void read_fault_env_locked() {
+    if (g_fault_env_read) return;
+    g_fault_env_read = true;
+    long a = -1, b = -1;
+    if (parse_fault_plan(std::getenv("AC_FAULT"), &a, &b)) {
+        g_fault_oom_at = a;
+        g_fault_launch_at = b;
+    }
+}
 
 bool inject_oom() {
     std::lock_guard<std::mutex> lk(g_fault_mu);
-    if (g_fault_oom_at == -2) {
-        g_fault_oom_at = -1;
-        const char* f = std::getenv("AC_FAULT");
-        if (f && std::strncmp(f, "oom@", 4) == 0) g_fault_oom_at = std::atol(f + 4);
-    }
+    read_fault_env_locked();
     ++g_alloc_count;
     return g_fault_oom_at > 0 && g_alloc_count == g_fault_oom_at;
 }
 
-cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t st) {
+// Device bytes held by the library's own synchronous allocations (machines,
+// streams, batch plans, tuner buffers), for ac_mem_usage.
+std::mutex g_live_mu;
+std::unordered_map<void*, size_t> g_live;
+uint64_t g_live_bytes = 0;
+
+}  // namespace
+
+bool ac_fault_launch() {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    read_fault_env_locked();
+    ++g_launch_count;
+    return g_fault_launch_at > 0 && g_launch_count == g_fault_launch_at;
+}
+
+cudaError_t ac_dev_alloc_async(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
     if (inject_oom()) return cudaErrorMemoryAllocation;
     return cudaMallocAsync(p, bytes, st);
 }
 
-cudaError_t dev_alloc(void** p, size_t bytes) {
+cudaError_t ac_dev_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
     if (inject_oom()) return cudaErrorMemoryAllocation;
-    return cudaMalloc(p, bytes);
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live[*p] = bytes;
+        g_live_bytes += bytes;
+    }
+    return e;
 }
+
+void ac_dev_free(void* p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        auto it = g_live.find(p);
+        if (it != g_live.end()) {
+            g_live_bytes -= it->second;
+            g_live.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
+extern "C" int ac_fault_inject(const char* spec) {
+    long a = -1, b = -1;
+    if (!parse_fault_plan(spec, &a, &b)) return AC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fault_env_read = true;  // an explicit plan replaces AC_FAULT
+    g_fault_oom_at = a;
+    g_fault_launch_at = b;
+    g_alloc_count = g_launch_count = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_mem_usage(ac_mem_usage_t* out) {
+    if (!out) return AC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof *out);
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        out->live_bytes = g_live_bytes;
+        out->live_allocations = (uint64_t)g_live.size();
+    }
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess)
+        return AC_ERR_CUDA;
+    uint64_t v = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) return AC_ERR_CUDA;
+    out->pool_used_bytes = v;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v) != cudaSuccess) return AC_ERR_CUDA;
+    out->pool_reserved_bytes = v;
+    {
+        std::lock_guard<std::mutex> lk(g_fault_mu);
+        out->allocations_seen = (uint64_t)g_alloc_count;
+        out->launches_seen = (uint64_t)g_launch_count;
+    }
+    return AC_OK;
+}
+
+namespace {
+
+cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t st) { return ac_dev_alloc_async(p, bytes, st); }
+cudaError_t dev_alloc(void** p, size_t bytes) { return ac_dev_alloc(p, bytes); }
 
 void keep_pool_memory() {
     static std::once_flag once[64];
@@ -221,14 +336,14 @@ extern "C" void ac_free(ac_dfa* d) {
         cudaGetDevice(&cur);
         if (d->device >= 0) cudaSetDevice(d->device);
         cudaDeviceSynchronize();
-        cudaFree(d->d_delta);
-        cudaFree(d->d_delta2);
-        cudaFree(d->d_delta3);
-        cudaFree(d->d_out_off);
-        cudaFree(d->d_out_ent);
-        cudaFree(d->d_gotos);
-        cudaFree(d->d_own_off);
-        cudaFree(d->d_own_ent);
+        ac_dev_free(d->d_delta);
+        ac_dev_free(d->d_delta2);
+        ac_dev_free(d->d_delta3);
+        ac_dev_free(d->d_out_off);
+        ac_dev_free(d->d_out_ent);
+        ac_dev_free(d->d_gotos);
+        ac_dev_free(d->d_own_off);
+        ac_dev_free(d->d_own_ent);
         cudaSetDevice(cur);
     }
     delete d;
@@ -346,9 +461,7 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     return sh;
 }
 
-namespace {
-
-bool valid_shape_opts(const ac_scan_opts* o) {
+bool ac_valid_shape_opts(const ac_scan_opts* o) {
     if (!o) return true;
     if (o->threads && (o->threads < 32 || o->threads > 1024 || o->threads % 32)) return false;
     if (o->interleave && o->interleave != 1 && o->interleave != 2 && o->interleave != 4 && o->interleave != 8)
@@ -357,6 +470,14 @@ bool valid_shape_opts(const ac_scan_opts* o) {
     if (o->stride > 3 || (o->stride == 2 && o->interleave == 8) || (o->stride == 3 && o->interleave > 2)) return false;
     return true;
 }
+
+bool ac_stride_tables_present(const ac_dfa* dfa, const ac_scan_opts* o) {
+    return !(o && ((o->stride == 2 && !dfa->d_delta2) || (o->stride == 3 && !dfa->d_delta3)));
+}
+
+namespace {
+
+bool valid_shape_opts(const ac_scan_opts* o) { return ac_valid_shape_opts(o); }
 
 size_t text_bytes(const ac_text& t) {
     return t.encoding == AC_TEXT_ASCII ? (size_t)t.n_bases : (size_t)((t.n_bases + 15) / 16) * 4;
@@ -901,7 +1022,7 @@ extern "C" int ac_stream_reset(ac_stream* s) {
 extern "C" void ac_stream_free(ac_stream* s) {
     if (!s) return;
     cudaDeviceSynchronize();
-    cudaFree(s->d_carry);
+    ac_dev_free(s->d_carry);
     delete s;
 }
 
@@ -1375,10 +1496,10 @@ extern "C" void ac_batch_plan_free(ac_batch_plan* p) {
     cudaDeviceSynchronize();
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    cudaFree(p->d_bt);
-    cudaFree(p->d_prefix);
-    cudaFree(p->d_ctr);
-    cudaFree(p->d_hits);
+    ac_dev_free(p->d_bt);
+    ac_dev_free(p->d_prefix);
+    ac_dev_free(p->d_ctr);
+    ac_dev_free(p->d_hits);
     if (p->h_pad) cudaFreeHost(p->h_pad);
     delete p;
 }

@@ -212,8 +212,34 @@ struct FlArgs {
     unsigned long long* hits;  // [S] own-keyword hits per state
 };
 int ac_launch_failureless(const FlArgs& a, uint32_t hot, void* stream);
+// Serving (ac_kernels.cu): splits the nm occurrences of a batch of n_req
+// requests (text_id = request index) per request on the device. n_per,
+// cursor [n_req] and req_counts [n_req * n_patterns] must be zero on entry.
+// Fills offs[0..n_req] (exclusive offsets of each request's range of out),
+// out (text_id 0) and req_counts (each request's per-keyword counts).
+int ac_launch_serve_split(const ac_match* in, uint64_t nm, uint32_t n_req, uint32_t n_patterns, ac_match* out,
+                          unsigned long long* req_counts, unsigned long long* n_per, unsigned long long* offs,
+                          unsigned long long* cursor, void* stream);
 // Sets the batch kernel's shared-memory limit for a shape (call before graph capture).
 int ac_prepare_batch(const ScanShape& sh);
+
+// Device allocations of the library (ac_api.cu): every one goes through these
+// so that host-side fault injection (ac_fault_inject) reaches it and
+// ac_mem_usage can account for what the library holds. ac_dev_alloc /
+// ac_dev_free are synchronous (cudaMalloc / cudaFree); ac_dev_alloc_async
+// takes stream-ordered pool memory (release it with cudaFreeAsync).
+cudaError_t ac_dev_alloc(void** p, size_t bytes);
+void ac_dev_free(void* p);
+cudaError_t ac_dev_alloc_async(void** p, size_t bytes, cudaStream_t st);
+// True when the fault plan says this kernel launch is to fail (the caller
+// then returns cudaErrorLaunchFailure without launching).
+bool ac_fault_launch();
+
+// Launch-shape options a scan accepts (threads, interleave, stride and their
+// compiled combinations), and whether the dfa has the table a requested
+// stride reads (ac_api.cu).
+bool ac_valid_shape_opts(const ac_scan_opts* o);
+bool ac_stride_tables_present(const ac_dfa* dfa, const ac_scan_opts* o);
 
 // Default / tuned shape selection (ac_api.cu / ac_tune.cpp)
 ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned_bases, const ac_scan_opts* opts);

@@ -967,6 +967,74 @@ __global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint2*
     }
 }
 
+// ---- serving: one batch's occurrences split per request, on the device.
+// Pass 1 counts every request's occurrences (n_per[t]) and its per-keyword
+// counts (req_counts[t * P + keyword]); pass 2 turns n_per into exclusive
+// offsets (one block); pass 3 writes each occurrence into its request's
+// range of `out` with text_id 0 (the order inside a range is free, as in any
+// scan result). Lanes of a warp that hold the same request combine their
+// atomics through __match_any_sync.
+__global__ void serve_count_kernel(const ac_match* __restrict__ in, uint64_t nm, uint32_t P,
+                                   unsigned long long* n_per, unsigned long long* req_counts) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = t0 - lane; base < nm; base += stride) {  // whole warps step together
+        const uint64_t i = base + lane;
+        const bool ok = i < nm;
+        const ac_match m = ok ? in[i] : ac_match{0, 0, 0xffffffffu};
+        const uint32_t peers = __match_any_sync(FULL, m.text_id);
+        if (ok) {
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&n_per[m.text_id], (unsigned long long)__popc(peers));
+            atomicAdd(&req_counts[(uint64_t)m.text_id * P + m.pattern_id], 1ull);
+        }
+    }
+}
+
+// offs[0..B]: exclusive prefix sums of n_per (one block of 1024 threads).
+__global__ void serve_offsets_kernel(const unsigned long long* __restrict__ n_per, uint32_t B,
+                                     unsigned long long* offs) {
+    __shared__ unsigned long long part[1024];
+    const uint32_t per = (B + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = threadIdx.x * per, b = min(B, a + per);
+    unsigned long long sum = 0;
+    for (uint32_t t = a; t < b; ++t) sum += n_per[t];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (uint32_t d = 1; d < blockDim.x; d <<= 1) {  // inclusive scan of the partial sums
+        const unsigned long long v = threadIdx.x >= d ? part[threadIdx.x - d] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - sum;
+    for (uint32_t t = a; t < b; ++t) {
+        offs[t] = run;
+        run += n_per[t];
+    }
+    if (threadIdx.x == blockDim.x - 1) offs[B] = part[threadIdx.x];
+}
+
+__global__ void serve_scatter_kernel(const ac_match* __restrict__ in, uint64_t nm,
+                                     const unsigned long long* __restrict__ offs, unsigned long long* cursor,
+                                     ac_match* __restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    for (uint64_t base = t0 - lane; base < nm; base += stride) {
+        const uint64_t i = base + lane;
+        const bool ok = i < nm;
+        const ac_match m = ok ? in[i] : ac_match{0, 0, 0xffffffffu};
+        const uint32_t peers = __match_any_sync(FULL, m.text_id);
+        const uint32_t leader = __ffs(peers) - 1;
+        unsigned long long first = 0;
+        if (ok && lane == leader) first = atomicAdd(&cursor[m.text_id], (unsigned long long)__popc(peers));
+        first = __shfl_sync(FULL, first, leader);
+        if (ok) out[offs[m.text_id] + first + __popc(peers & lt)] = ac_match{m.pos, m.pattern_id, 0u};
+    }
+}
+
 // Raises a kernel's dynamic shared-memory limit to `bytes`; the driver call is
 // skipped when this device already has a limit at least that high for this
 // kernel (keyed by the kernel's address: kernels of one signature share a type).
@@ -1122,6 +1190,7 @@ struct ScanLaunch {
         const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
         int rc = set_smem(scan_kernel<I, ST, W>, smem);
         if (rc) return rc;
+        if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
         scan_kernel<I, ST, W><<<sh.grid, sh.threads, smem, st>>>(a, sh.chunk, sh.hot, n_chunks);
         return (int)cudaGetLastError();
     }
@@ -1144,6 +1213,7 @@ struct BatchLaunch {
         const size_t smem = ac_scan_smem_bytes(sh.hot, sh.threads, ST);
         int rc = set_smem(batch_kernel<I, ST, W>, smem);
         if (rc || prepare_only) return rc;
+        if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
         batch_kernel<I, ST, W><<<sh.grid, sh.threads, smem, st>>>(a, sh.hot);
         return (int)cudaGetLastError();
     }
@@ -1187,6 +1257,7 @@ int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold
     const uint64_t cap = (uint64_t)p.sms * (uint64_t)resident.load();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
     pack_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ascii, n, packed, fold ? 1 : 0, bad);
     return (int)cudaGetLastError();
 }
@@ -1224,6 +1295,7 @@ int ac_launch_part_scan(const PartArgs& a, uint32_t n_parts, uint32_t grid_x, ui
     const size_t smem = ac_scan_smem_bytes(a.max_states, threads, 1);
     int rc = set_smem(part_scan_kernel<1>, smem);
     if (rc) return rc;
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
     part_scan_kernel<1><<<dim3(grid_x, n_parts), threads, smem, (cudaStream_t)stream>>>(a, chunk, n_chunks);
     return (int)cudaGetLastError();
 }
@@ -1239,6 +1311,7 @@ int ac_launch_failureless(const FlArgs& a, uint32_t hot, void* stream) {
     const uint64_t span = a.own_end - (a.own_begin > a.halo ? a.own_begin - a.halo : 0);
     const uint64_t want = (span + 1023) / 1024;
     const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)p.sms * std::max(nb, 1));
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
     failureless_kernel<<<grid, 1024, smem, (cudaStream_t)stream>>>(a, hot);
     return (int)cudaGetLastError();
 }
@@ -1251,6 +1324,7 @@ int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint6
     uint64_t blocks = (words + 255) / 256;
     const uint64_t cap = (uint64_t)p.sms * 8;
     if (blocks > cap) blocks = cap;
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
     splice_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(dst, dst_off, src, src_off, n);
     return (int)cudaGetLastError();
 }
@@ -1262,6 +1336,27 @@ int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_s
     uint32_t blocks = (n_states + 255) / 256;
     const uint32_t cap = (uint32_t)p.sms * 8;
     if (blocks > cap) blocks = cap;
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
     counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_ent, n_states, hits, counts);
+    return (int)cudaGetLastError();
+}
+
+int ac_launch_serve_split(const ac_match* in, uint64_t nm, uint32_t n_req, uint32_t n_patterns, ac_match* out,
+                          unsigned long long* req_counts, unsigned long long* n_per, unsigned long long* offs,
+                          unsigned long long* cursor, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const DeviceProps& p = ac_device_props();
+    const uint64_t want = (nm + 255) / 256;
+    const uint32_t blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)p.sms * 8));
+    if (nm) {
+        if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
+        serve_count_kernel<<<blocks, 256, 0, st>>>(in, nm, n_patterns, n_per, req_counts);
+    }
+    if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
+    serve_offsets_kernel<<<1, 1024, 0, st>>>(n_per, n_req, offs);
+    if (nm) {
+        if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
+        serve_scatter_kernel<<<blocks, 256, 0, st>>>(in, nm, offs, cursor, out);
+    }
     return (int)cudaGetLastError();
 }

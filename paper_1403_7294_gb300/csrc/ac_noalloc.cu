@@ -60,15 +60,8 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     if (text->n_bases && (!text->data || (reinterpret_cast<uintptr_t>(text->data) & 15))) return AC_ERR_INVALID_ARG;
     if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
-    if (opts && opts->threads && (opts->threads < 32 || opts->threads > 1024 || opts->threads % 32))
-        return AC_ERR_INVALID_ARG;
-    if (opts && opts->interleave && opts->interleave != 1 && opts->interleave != 2 && opts->interleave != 4 &&
-        opts->interleave != 8)
-        return AC_ERR_INVALID_ARG;
-    if (opts && opts->threads && opts->threads > ac_max_threads(opts->interleave ? opts->interleave : 1))
-        return AC_ERR_INVALID_ARG;
-    if (opts && (opts->stride > 2 || (opts->stride == 2 && (opts->interleave == 8 || !dfa->d_delta2))))
-        return AC_ERR_INVALID_ARG;
+    // the launch-shape options ac_scan accepts, and the table a requested stride reads
+    if (!ac_valid_shape_opts(opts) || !ac_stride_tables_present(dfa, opts)) return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;
     if (h.n_states > kMaxStates) return AC_ERR_TOO_LARGE;  // the fixed scratch is too small
     const uint64_t n = text->n_bases;

@@ -10,14 +10,19 @@
 // meantime, so scans of different sizes overlap on the device.
 //
 // A request's device bytes: its packed text (n/4), its ASCII text if it came
-// as ASCII (n), and its output reservation (16 B per reserved occurrence). The
-// reservation per base is learned per dfa from the batches it has served
-// (twice the densest seen, decaying slowly), so batches rarely outgrow it.
+// as ASCII (n), its output reservation (16 B per reserved occurrence, twice:
+// the batch's output and the per-request split of it) and its per-keyword
+// counts (8 B per keyword of its dfa). The reservation per base is learned
+// per dfa from the batches it has served (twice the densest seen, decaying
+// slowly), so batches rarely outgrow it.
 // Per-request results are exactly the stand-alone scan's: the batch writes
-// every occurrence with its text index, the worker splits them per request,
-// and per-keyword counts are the histogram of each request's occurrences. If
-// a batch overflows its reservation (its occurrence count is still exact),
-// the batch runs once more with exactly that much room.
+// every occurrence with its text index; for a batch of several requests two
+// device passes split them into one range per request and count each
+// request's occurrences per keyword (no host loop over occurrences), and one
+// copy brings all of it into a pinned block the batch's requests share. A
+// batch of one request takes the batch's own counts. If a batch overflows
+// its reservation (its occurrence count is still exact), the batch runs once
+// more with exactly that much room.
 //
 // Host copies are what a large request's latency is made of, so texts of
 // 1 MiB or more are copied at submit into pinned blocks from a pool and go to
@@ -118,12 +123,15 @@ struct Request {
     std::vector<ac_match> matches;
     std::vector<uint64_t> counts;
     uint64_t n_matches = 0;
-    // a batch of one leaves its results in a pinned block instead: n_matches
-    // occurrences, then the counts
+    // or in a pinned block the request holds (shared by the requests of one
+    // batch): n_matches occurrences at match_off, the counts at count_off
     std::shared_ptr<PinnedPool::Block> block;
-    const ac_match* match_data() const { return block ? (const ac_match*)block->p : matches.data(); }
+    size_t match_off = 0, count_off = 0;  // bytes into block
+    const ac_match* match_data() const {
+        return block ? (const ac_match*)((const uint8_t*)block->p + match_off) : matches.data();
+    }
     const uint64_t* count_data() const {
-        return block ? (const uint64_t*)((const uint8_t*)block->p + n_matches * sizeof(ac_match)) : counts.data();
+        return block ? (const uint64_t*)((const uint8_t*)block->p + count_off) : counts.data();
     }
     size_t n_counts = 0;
 };
@@ -235,6 +243,8 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     uint32_t* d_packed = nullptr;
     ac_match* d_m = nullptr;
     unsigned long long* d_cnt = nullptr;
+    ac_match* d_split = nullptr;              // several requests: the occurrences split per request
+    unsigned long long* d_aux_keep = nullptr;  // their offsets, cursors and per-request counts
     auto fail_all = [&](int s) { status = s; };
 
     // ---- stage: ASCII bytes padded with 'A', then packed words (texts held in
@@ -254,9 +264,9 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
                 std::memcpy(h_packed + slot[i] / 4 - ascii_bases / 4, r.bytes.data(), wb);
             }
         }
-        if (cudaMallocAsync((void**)&d_packed, std::max<size_t>(packed_bytes, 16), st) != cudaSuccess ||
-            (ascii_bases && cudaMallocAsync((void**)&d_ascii, ascii_bases, st) != cudaSuccess) ||
-            cudaMallocAsync((void**)&d_m, std::max<uint64_t>(reserve, 1) * sizeof(ac_match), st) != cudaSuccess)
+        if (ac_dev_alloc_async((void**)&d_packed, std::max<size_t>(packed_bytes, 16), st) != cudaSuccess ||
+            (ascii_bases && ac_dev_alloc_async((void**)&d_ascii, ascii_bases, st) != cudaSuccess) ||
+            ac_dev_alloc_async((void**)&d_m, std::max<uint64_t>(reserve, 1) * sizeof(ac_match), st) != cudaSuccess)
             fail_all(AC_ERR_OOM);
     }
     if (status == AC_OK) {
@@ -304,17 +314,18 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
         res.matches = d_m;
         res.capacity = reserve;
         res.on_device = 1;
-        // a batch of one: the batch's counts are the request's counts (no histogram on the host)
-        if (B == 1 && cudaMallocAsync((void**)&d_cnt, (size_t)P * 8, st) != cudaSuccess) d_cnt = nullptr;
+        // a batch of one: the batch's counts are the request's counts
+        int s = AC_OK;
+        if (B == 1 && ac_dev_alloc_async((void**)&d_cnt, (size_t)P * 8, st) != cudaSuccess) s = AC_ERR_OOM;
         res.counts = (uint64_t*)d_cnt;
-        int s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
+        if (s == AC_OK) s = ac_scan_batch(dfa, texts.data(), (uint32_t)B, &res, nullptr, st, nullptr);
         nm = res.n_matches;
         if (s == AC_ERR_OVERFLOW) {
             // more occurrences than reserved: the count is exact, so the batch runs once more with room for all
             overflowed = true;
             cudaFreeAsync(d_m, st);
             d_m = nullptr;
-            if (cudaMallocAsync((void**)&d_m, std::max<uint64_t>(nm, 1) * sizeof(ac_match), st) != cudaSuccess) {
+            if (ac_dev_alloc_async((void**)&d_m, std::max<uint64_t>(nm, 1) * sizeof(ac_match), st) != cudaSuccess) {
                 s = AC_ERR_OOM;
             } else {
                 res.matches = d_m;
@@ -328,30 +339,32 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
             fail_all(s);
         } else {
             const size_t mb = nm * sizeof(ac_match);
-            // one request with many occurrences: they (with text index 0 already)
-            // and the batch's counts, which are the request's, land in a pinned
-            // block the request keeps until it is waited for; no copy on the host
-            std::shared_ptr<PinnedPool::Block> blk;
-            if (d_cnt && mb >= kHandoffBytes) blk = pool->get(mb + (size_t)P * 8);  // none: the worker's buffer
-            const bool handoff = blk != nullptr;
-            void* dst = nullptr;
-            if (handoff) {
-                dst = blk->p;
-            } else if (results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
-                dst = results.p;
-            }
-            if (!dst) {
-                fail_all(AC_ERR_OOM);
-            } else {
-                if (nm) cudaMemcpyAsync(dst, d_m, mb, cudaMemcpyDeviceToHost, st);
-                if (d_cnt) cudaMemcpyAsync((uint8_t*)dst + mb, d_cnt, (size_t)P * 8, cudaMemcpyDeviceToHost, st);
-                if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
-            }
-            if (status == AC_OK && d_cnt) {
+            if (B == 1) {
+                // one request: the batch's occurrences (text index 0 already) and
+                // counts are the request's. With many occurrences they land in a
+                // pinned block the request keeps until it is waited for.
+                std::shared_ptr<PinnedPool::Block> blk;
+                if (d_cnt && mb >= kHandoffBytes) blk = pool->get(mb + (size_t)P * 8);  // none: the worker's buffer
+                const bool handoff = blk != nullptr;
+                void* dst = nullptr;
+                if (handoff) {
+                    dst = blk->p;
+                } else if (results.ensure(std::max<size_t>(mb + (d_cnt ? (size_t)P * 8 : 0), 16))) {
+                    dst = results.p;
+                }
+                if (!dst) {
+                    fail_all(AC_ERR_OOM);
+                } else {
+                    if (nm) cudaMemcpyAsync(dst, d_m, mb, cudaMemcpyDeviceToHost, st);
+                    if (d_cnt) cudaMemcpyAsync((uint8_t*)dst + mb, d_cnt, (size_t)P * 8, cudaMemcpyDeviceToHost, st);
+                    if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
+                }
                 Request& r = *batch[0];
-                if (r.status == AC_OK) {
+                if (status == AC_OK && r.status == AC_OK) {
                     if (handoff) {
                         r.block = std::move(blk);
+                        r.match_off = 0;
+                        r.count_off = mb;
                     } else {
                         const ac_match* m = (const ac_match*)dst;
                         const uint64_t* c = (const uint64_t*)((const uint8_t*)dst + mb);
@@ -361,28 +374,60 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
                     r.n_matches = nm;
                     r.n_counts = P;
                 }
-            }
-            if (status == AC_OK && !d_cnt) {
-                // split per request (counting sort by text index)
-                const ac_match* m = (const ac_match*)dst;
-                std::vector<uint64_t> per(B, 0);
-                for (uint64_t k = 0; k < nm; ++k) per[m[k].text_id]++;
-                for (size_t i = 0; i < B; ++i) {
-                    Request& r = *batch[i];
-                    if (r.status != AC_OK) continue;
-                    r.matches.clear();
-                    r.matches.reserve(per[i]);
-                    r.counts.assign(P, 0);
-                    r.n_matches = per[i];
-                    r.n_counts = P;
-                }
-                for (uint64_t k = 0; k < nm; ++k) {
-                    Request& r = *batch[m[k].text_id];
-                    if (r.status != AC_OK) continue;
-                    ac_match x = m[k];
-                    x.text_id = 0;
-                    r.matches.push_back(x);
-                    r.counts[x.pattern_id]++;
+            } else {
+                // several requests: split on the device (each request's occurrences
+                // in one range, its per-keyword counts in a row of B x P), then one
+                // copy into a pinned block the batch's requests share
+                const size_t cb = (size_t)B * P * 8, ob = (B + 1) * sizeof(unsigned long long);
+                unsigned long long* d_aux = nullptr;  // [n_per B][cursor B][offs B+1][counts B*P]
+                const size_t aux = (3 * (size_t)B + 1) * 8 + cb;
+                if (ac_dev_alloc_async((void**)&d_split, std::max<size_t>(mb, 16), st) != cudaSuccess ||
+                    ac_dev_alloc_async((void**)&d_aux, aux, st) != cudaSuccess) {
+                    fail_all(AC_ERR_OOM);
+                } else {
+                    d_aux_keep = d_aux;
+                    unsigned long long* n_per = d_aux;
+                    unsigned long long* cursor = d_aux + B;
+                    unsigned long long* offs = d_aux + 2 * B;
+                    unsigned long long* rc = d_aux + 3 * B + 1;
+                    if (cudaMemsetAsync(d_aux, 0, aux, st) != cudaSuccess) fail_all(AC_ERR_CUDA);
+                    if (status == AC_OK &&
+                        ac_launch_serve_split(d_m, nm, (uint32_t)B, P, d_split, rc, n_per, offs, cursor, st) != 0)
+                        fail_all(AC_ERR_CUDA);
+                    std::shared_ptr<PinnedPool::Block> blk;
+                    void* dst = nullptr;
+                    if (status == AC_OK) {
+                        blk = pool->get(mb + cb + ob);
+                        if (blk) dst = blk->p;
+                        else if (results.ensure(mb + cb + ob)) dst = results.p;  // no pooled block: the worker's
+                        if (!dst) fail_all(AC_ERR_OOM);
+                    }
+                    if (status == AC_OK) {
+                        if (nm) cudaMemcpyAsync(dst, d_split, mb, cudaMemcpyDeviceToHost, st);
+                        cudaMemcpyAsync((uint8_t*)dst + mb, rc, cb, cudaMemcpyDeviceToHost, st);
+                        cudaMemcpyAsync((uint8_t*)dst + mb + cb, offs, ob, cudaMemcpyDeviceToHost, st);
+                        if (cudaStreamSynchronize(st) != cudaSuccess) fail_all(AC_ERR_CUDA);
+                    }
+                    if (status == AC_OK) {
+                        const uint64_t* off = (const uint64_t*)((const uint8_t*)dst + mb + cb);
+                        for (size_t i = 0; i < B; ++i) {
+                            Request& r = *batch[i];
+                            if (r.status != AC_OK) continue;
+                            r.n_matches = off[i + 1] - off[i];
+                            r.n_counts = P;
+                            const size_t mo = off[i] * sizeof(ac_match), co = mb + i * (size_t)P * 8;
+                            if (blk) {
+                                r.block = blk;
+                                r.match_off = mo;
+                                r.count_off = co;
+                            } else {
+                                const ac_match* m = (const ac_match*)((const uint8_t*)dst + mo);
+                                const uint64_t* c = (const uint64_t*)((const uint8_t*)dst + co);
+                                r.matches.assign(m, m + r.n_matches);
+                                r.counts.assign(c, c + P);
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -391,6 +436,8 @@ void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>
     if (d_packed) cudaFreeAsync(d_packed, st);
     if (d_m) cudaFreeAsync(d_m, st);
     if (d_cnt) cudaFreeAsync(d_cnt, st);
+    if (d_split) cudaFreeAsync(d_split, st);
+    if (d_aux_keep) cudaFreeAsync(d_aux_keep, st);
     cudaStreamSynchronize(st);
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(mu);
@@ -525,7 +572,7 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
         const double per_base = std::max(s->opts.match_capacity_per_base_x1000 / 1000.0, s->density[slot]);
         r->reserve = (uint64_t)((double)t->n_bases * per_base) + 1024;
         r->dev_bytes = round_up(t->n_bases, 64) / 4 + (t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : 0) +
-                       r->reserve * sizeof(ac_match);
+                       2 * r->reserve * sizeof(ac_match) + (uint64_t)s->dfas[slot]->host.n_patterns * 8;
         if (s->stop || s->pending.size() >= s->opts.max_queue || r->dev_bytes > s->opts.device_budget_bytes) {
             s->rejected++;
             return AC_ERR_BUSY;

@@ -172,7 +172,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
         cap = std::min<uint64_t>(r0.n_matches + 1024, free_b / 2 / sizeof(ac_match));
     }
     ac_match* d_m = nullptr;
-    if (cudaMalloc(&d_m, std::max<uint64_t>(cap, 1) * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
+    if (ac_dev_alloc((void**)&d_m, std::max<uint64_t>(cap, 1) * sizeof(ac_match)) != cudaSuccess) return AC_ERR_OOM;
 
     const uint32_t threads_c[] = {256, 512, 0, 768, 1024};  // 0: the two-blocks-per-SM build's size, if any
     const uint32_t inter_c[] = {1, 2, 4, 8};
@@ -224,7 +224,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
                                  il, hot, t_best);
                 if (t_best < top.ms) top = Entry{th, il, hot, sd, t_best};
             }
-    cudaFree(d_m);
+    ac_dev_free(d_m);
     if (rc != AC_OK) return rc;
     if (top.threads == 0) return AC_ERR_CUDA;
     {

@@ -391,3 +391,13 @@ def test_build_entry_leaves_the_public_build_function():
     assert callable(acg.build)
     d = acg.build([b"ACGT", b"CG"], host_only=True)
     assert d.info["n_states"] == 7  # root, A, AC, ACG, ACGT, C, CG
+
+
+def test_fault_plan_parsing_on_the_host():
+    """ac_fault_inject needs no GPU: it only sets the host-side plan (cleared again here)."""
+    lib = acg.lib()
+    for spec in (b"oom@1", b"cuda_err@7", b"oom@3,cuda_err@2", b""):
+        assert lib.ac_fault_inject(spec) == N.AC_OK
+    for bad in (b"oom", b"oom@0", b"oom@-2", b"oom@x", b"leak@1", b"oom@1;cuda_err@2", b"oom@1,"):
+        assert lib.ac_fault_inject(bad) == N.AC_ERR_INVALID_ARG
+    assert lib.ac_fault_inject(None) == N.AC_OK

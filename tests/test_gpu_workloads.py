@@ -1,18 +1,21 @@
 """GPU parity on the benchmark workloads at their full sizes, in the launch
-configuration the benchmark times (the library's default shape).
+configuration the benchmark times (the autotuned shape, as the benchmark
+picks it).
 
   * 256 Mbase Markov chromosome, 10,000 keywords: every occurrence against
     the oracle's full scan, at one, two and three bases per lookup;
-  * 3 Gbase Markov genome, 100,000 keywords: occurrences in 24 sampled
-    windows against the oracle run on each window (with the L_max-1 halo),
-    plus properties that hold at any size (counts = histogram of the list,
-    sum of counts = occurrences, the same set under launch shapes reading
-    two and three bases per lookup);
+  * 3 Gbase Markov genome, 100,000 keywords: every occurrence and every
+    per-keyword count against the oracle. The text is cut into 64 ranges of
+    start positions; the oracle scans each range plus the L_max-1 bases after
+    it (all host cores, one range per thread) and keeps the occurrences that
+    start inside it, while the GPU's occurrences, sorted on the device by
+    (start, keyword), are read back one range at a time. The same set comes
+    out under launch shapes reading one, two and three bases per lookup;
   * 4,096 lognormal texts, 50,000 keywords: the graph-replayed batch and the
     per-text loop against the oracle on every text;
-  * the 8 serving sets: requests alone and mixed against the oracle.
+  * the 8 serving sets: every request alone and in the mix against the oracle.
 """
-import random
+import os
 
 import numpy as np
 import pytest
@@ -45,60 +48,68 @@ def test_chromosome_full_parity():
     assert r.n_matches > 5000  # the substring half of the keywords occurs
 
 
-def test_genome_sampled_parity_and_invariants():
+PID_BITS = 17  # keyword ids of the genome workload are below 2^17
+
+
+def _sorted_keys(pos: torch.Tensor, pid: torch.Tensor) -> torch.Tensor:
+    """(start, keyword) pairs as one sorted int64 key per occurrence, on the device."""
+    return torch.sort(pos * (1 << PID_BITS) + pid)[0]
+
+
+def test_genome_full_parity_against_the_oracle():
+    from concurrent.futures import ThreadPoolExecutor
+
     w = synth.plain_genome(device="cuda")
     n = w.text.ascii.numel()
+    P = len(w.patterns)
+    assert P < (1 << PID_BITS)
     d = acg.build(w.patterns)
     packed = acg.pack(w.text.ascii)
-    lens = torch.tensor([len(p) for p in w.patterns], dtype=torch.int64, device="cuda")
-    lmax = int(lens.max())
+    lmax = max(len(p) for p in w.patterns)
+    acg.autotune(d, packed, n)  # the benchmark's launch shape
     r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=1 << 20)
     k = r.n_matches
     assert k > 1_000_000  # repeat-driven density
-    # any-size properties
     assert int(r.counts.sum()) == k
-    hist = torch.bincount(r.pattern_id, minlength=len(w.patterns))
-    assert torch.equal(hist, r.counts)
-    # the same set under a second launch shape (two bases per lookup, small chunks, nothing in shared memory)
-    r2 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, chunk=4096,
-                  hot_states=0, stride=2)
-    assert r2.n_matches == k
-    a = torch.sort(_keys(r.pos, r.pattern_id))[0]
-    b = torch.sort(_keys(r2.pos, r2.pattern_id))[0]
-    assert torch.equal(a, b)
-    del r2, b
-    # and three bases per lookup, in one 1024-thread block per SM and in two 640-thread blocks
-    for threads in (1024, 640):
-        r3 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, interleave=1, stride=3,
-                      threads=threads)
-        assert r3.n_matches == k
-        assert torch.equal(a, torch.sort(_keys(r3.pos, r3.pattern_id))[0])
-        assert torch.equal(r.counts, r3.counts)
-        del r3
-    assert torch.equal(r.counts, acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=0,
-                                          interleave=2, stride=1).counts)
-    # sampled windows against the oracle
-    end = r.pos + lens[r.pattern_id] - 1
-    rng = random.Random(2024)
+    keys = _sorted_keys(r.pos, r.pattern_id)
+    counts = r.counts.cpu().numpy()
+    del r
+    # the same set under other launch shapes: one base per lookup with two chains per lane and small
+    # chunks, two bases per lookup, three bases per lookup in one 1024-thread block per SM
+    for kw in ({"stride": 1, "interleave": 2, "chunk": 4096}, {"stride": 2, "interleave": 1, "hot_states": 0},
+               {"stride": 3, "interleave": 1, "threads": 1024}):
+        r2 = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=n, capacity=k + 16, **kw)
+        assert r2.n_matches == k, kw
+        assert torch.equal(keys, _sorted_keys(r2.pos, r2.pattern_id)), kw
+        assert np.array_equal(r2.counts.cpu().numpy(), counts), kw
+        del r2
+    # every occurrence against the oracle, 64 ranges of start positions on all host cores
+    text = w.text.ascii.cpu().numpy()
+    del w.text.ascii, packed
     m = oracle.Machine(w.patterns)
-    lens_h = lens.cpu().numpy()
-    starts = sorted(rng.sample(range(0, n - 2_000_000), 22)) + [0, n - 2_000_000]
+    W = 64
+    bounds = [n * i // W for i in range(W + 1)]
+
+    def oracle_range(i):
+        s0, s1 = bounds[i], bounds[i + 1]
+        pos, pid, _ = m.scan(text[s0 : min(n, s1 + lmax - 1)])
+        start = pos.astype(np.int64) + s0
+        keep = start < s1  # every occurrence starting in [s0, s1) ends before s1 + lmax - 1
+        pid = pid[keep].astype(np.int64)
+        return np.sort((start[keep] << PID_BITS) | pid), np.bincount(pid, minlength=P)
+
+    want_counts = np.zeros(P, np.int64)
     total = 0
-    for s0 in starts:
-        s1 = s0 + 2_000_000
-        rb = max(0, s0 - (lmax - 1))
-        win = w.text.ascii[rb:s1].cpu().numpy()
-        pos, pid, _ = m.scan(win)
-        e = pos.astype(np.int64) + lens_h[pid] - 1 + rb
-        keep = e >= s0
-        want = np.stack([pos[keep].astype(np.int64) + rb, pid[keep].astype(np.int64)], 1)
-        want = want[np.lexsort((want[:, 1], want[:, 0]))]
-        sel = (end >= s0) & (end < s1)
-        got = torch.stack([r.pos[sel], r.pattern_id[sel]], 1).cpu().numpy()
-        got = got[np.lexsort((got[:, 1], got[:, 0]))]
-        assert np.array_equal(got, want), f"window {s0}"
-        total += len(want)
-    assert total > 0
+    with ThreadPoolExecutor(max_workers=min(W, os.cpu_count() or 4)) as ex:
+        for i, (want, c) in enumerate(ex.map(oracle_range, range(W))):
+            lo = int(torch.searchsorted(keys, torch.tensor([bounds[i] << PID_BITS], device=keys.device)))
+            hi = int(torch.searchsorted(keys, torch.tensor([bounds[i + 1] << PID_BITS], device=keys.device)))
+            got = keys[lo:hi].cpu().numpy()
+            assert got.shape == want.shape and np.array_equal(got, want), f"range {i} [{bounds[i]}, {bounds[i + 1]})"
+            want_counts += c
+            total += len(want)
+    assert total == k
+    assert np.array_equal(counts, want_counts)
 
 
 def test_batched_full_parity():
@@ -125,6 +136,10 @@ def test_batched_full_parity():
 
 
 def test_serving_sets_alone_vs_mix():
+    """Every one of 48 requests: submitted together (batched with others of its machine while other
+    batches run), then alone, then against the oracle."""
+    from concurrent.futures import ThreadPoolExecutor
+
     genome = synth.markov_text(8 << 20, synth.BASE_SEED + 4, device="cuda")
     sets = synth.serve_sets(genome.ascii)
     g = genome.ascii.cpu().numpy()
@@ -134,12 +149,24 @@ def test_serving_sets_alone_vs_mix():
     slots = [srv.add_dfa(x) for x in dfas]
     tks = [srv.submit(slots[s], g[o : o + n]) for s, o, n in zip(which, offs, lens)]
     mix = [srv.wait(t, slots[s], capacity=4096) for t, s in zip(tks, which)]
-    for i in range(0, 48, 6):  # a subset alone and against the oracle
+    st = srv.stats()
+    assert st["completed"] == 48 and st["failed"] == 0
+    machines = {s: oracle.Machine(sets[s]) for s in set(int(x) for x in which)}  # shared by the threads (read only)
+
+    def want_of(i):
+        s, o, n = int(which[i]), int(offs[i]), int(lens[i])
+        pos, pid, c = machines[s].scan(g[o : o + n])
+        a = np.stack([pos.astype(np.int64), pid.astype(np.int64)], 1)
+        return a[np.lexsort((a[:, 1], a[:, 0]))], c.astype(np.int64)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        wants = list(ex.map(want_of, range(48)))
+    for i in range(48):
         s, o, n = int(which[i]), int(offs[i]), int(lens[i])
         alone = srv.wait(srv.submit(slots[s], g[o : o + n]), slots[s])
         a = alone[0][np.lexsort((alone[0][:, 1], alone[0][:, 0]))]
         b = mix[i][0][np.lexsort((mix[i][0][:, 1], mix[i][0][:, 0]))]
-        assert np.array_equal(a, b) and np.array_equal(alone[1], mix[i][1])
-        want, counts = oracle_canonical(sets[s], g[o : o + n])
-        assert np.array_equal(a, want[:, 1:]) and np.array_equal(alone[1], counts)
+        want, counts = wants[i]
+        assert np.array_equal(b, want) and np.array_equal(mix[i][1], counts), f"request {i} in the mix"
+        assert np.array_equal(a, want) and np.array_equal(alone[1], counts), f"request {i} alone"
     srv.close()

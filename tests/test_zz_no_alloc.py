@@ -5,9 +5,11 @@ memory is already held by another allocator, or they run a loop that must
 not enter an allocator); it uses the library's fixed scratch array instead
 of pool memory. This file is collected last on purpose, so that a run that
 stops at the first failure has run every other test before it. Each check
-compares the call with ac_scan on the same inputs, exactly (all results are
-integers), over two calls in a row: the scratch array keeps the previous
-call's contents, so the second call shows that it is cleared correctly.
+compares the call with ac_scan on the same inputs, and with the CPU oracle,
+exactly (all results are integers), over two calls in a row: the scratch
+array keeps the previous call's contents, so the second call shows that it
+is cleared correctly. The launch-shape options are those of ac_scan, so one,
+two and three bases per lookup are all checked.
 """
 import ctypes
 import random
@@ -18,6 +20,7 @@ import torch
 
 import paper_1403_7294_gb300 as acg
 from paper_1403_7294_gb300 import _native as N
+from tests.gpu_helpers import oracle_canonical
 
 pytestmark = pytest.mark.gpu
 
@@ -50,12 +53,36 @@ def test_noalloc_equals_ac_scan_on_two_calls_in_a_row():
         ref = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text))
         want = ref.canonical()[:, 1:]
         want_counts = ref.counts.cpu().numpy()
+        orc, orc_counts = oracle_canonical(pats, np.frombuffer(text, np.uint8))
+        assert np.array_equal(want, orc[:, 1:]) and np.array_equal(want_counts, orc_counts)
         for _ in range(2):
             st, got, counts, k = _noalloc(d, packed, len(text), ref.n_matches + 8)
             assert st == N.AC_OK
             assert k == ref.n_matches
             assert np.array_equal(got, want)
             assert np.array_equal(counts, want_counts)
+
+
+def test_noalloc_every_stride_against_the_oracle():
+    text, pats = _case(4, 400_000, 1500)
+    d = acg.build(pats)
+    packed = acg.pack(torch.tensor(np.frombuffer(text, np.uint8), device="cuda"))
+    orc, orc_counts = oracle_canonical(pats, np.frombuffer(text, np.uint8))
+    for stride, threads, interleave in ((1, 0, 0), (2, 0, 0), (3, 0, 0), (3, 640, 1), (3, 512, 2)):
+        o = N.ScanOpts()
+        o.hot_states, o.stride, o.threads, o.interleave = -1, stride, threads, interleave
+        for _ in range(2):
+            st, got, counts, k = _noalloc(d, packed, len(text), len(orc) + 8, o)
+            assert st == N.AC_OK, (stride, threads, interleave, st)
+            assert k == len(orc) and np.array_equal(got, orc[:, 1:]), (stride, threads, interleave)
+            assert np.array_equal(counts, orc_counts)
+    # a stride whose table was not built is refused, as by ac_scan
+    d1 = acg.build(pats, stride2=False, stride3=False)
+    for stride in (2, 3):
+        o = N.ScanOpts()
+        o.hot_states, o.stride = -1, stride
+        st, _, _, _ = _noalloc(d1, packed, len(text), 16, o)
+        assert st == N.AC_ERR_INVALID_ARG
 
 
 def test_noalloc_owned_range_and_overflow():
