@@ -385,12 +385,42 @@ def run_plain(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     assert int(res_h.n_matches) == n_matches and int(cnt_h.sum()) == n_matches
+    h2d_bytes, d2h_bytes = int(host_packed.numel() * 4), int(16 * n_matches + 8 * P + 16)
+    # the host link in the same run: pinned copies of the same sizes, timed with CUDA events
+    link = host_link_bandwidth(host_packed, raw_h, raw, stream)
+    floor_ms = max(h2d_bytes / (link["h2d_gbs"] * 1e6), d2h_bytes / (link["d2h_gbs"] * 1e6))
+    med = float(np.median(call_ms))
     out["e2e"] = {"value": round(k_e2e * n * world / e2e_s / 1e9, 3), "unit": UNIT,
-                  "h2d_bytes_per_step": int(host_packed.numel() * 4),
-                  "d2h_bytes_per_step": int(16 * n_matches + 8 * P + 16), "steps": k_e2e, "call_ms": call_ms,
-                  "median_call_ms": float(np.median(call_ms))}
+                  "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes, "steps": k_e2e,
+                  "call_ms": call_ms, "median_call_ms": med, "max_call_ms": float(np.max(call_ms)),
+                  "value_at_median_call": round(n * world / (med / 1e3) / 1e9, 3),
+                  # the call overlaps its copies in and out with the scan: the longer copy bounds it
+                  "roofline": {"bound": "host link (pinned copies)", "h2d_gbs": link["h2d_gbs"],
+                               "d2h_gbs": link["d2h_gbs"], "copy_floor_ms": round(floor_ms, 3),
+                               "frac": round(floor_ms / med, 4), "how": link["how"]}}
     del host_packed, raw_h
     return out, (dfa, w, ascii_prefix)
+
+
+def host_link_bandwidth(host_src: torch.Tensor, host_dst: torch.Tensor, dev_src: torch.Tensor, stream) -> dict:
+    """Pinned host-to-device and device-to-host copy bandwidth (GB/s), each the best of three copies of
+    the given buffers' sizes, timed with CUDA events on the stream."""
+    dev_dst = torch.empty(host_src.numel(), dtype=host_src.dtype, device="cuda")
+    res = {}
+    for name, dst, src in (("h2d_gbs", dev_dst, host_src), ("d2h_gbs", host_dst, dev_src)):
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        res[name] = round(src.numel() * src.element_size() / (best / 1e3) / 1e9, 2)
+    res["how"] = (f"best of 3 pinned copies: {host_src.numel() * host_src.element_size() / 1e6:.0f} MB in, "
+                  f"{dev_src.numel() * dev_src.element_size() / 1e6:.0f} MB out, CUDA events")
+    del dev_dst
+    return res
 
 
 # ------------------------------------------------------ lookup roofline
@@ -566,6 +596,11 @@ def run_cpu_sweep(args, rank):
 
 
 def run_batched(args, steps: int):
+    """The batch workload: one graph-replayed persistent launch over the 4,096 texts against a per-text
+    loop of ac_scan. Both sides are timed on one clock at a time: device time by CUDA events (the plan's
+    replays against the sum of every loop call's own event-timed device time, and the batch kernel
+    against the sum of the loop's scan-kernel times) and host wall time (ac_scan_batch calls against the
+    loop's calls, each of which waits for its count)."""
     import ctypes
 
     import paper_1403_7294_gb300 as acg
@@ -578,8 +613,9 @@ def run_batched(args, steps: int):
     total = int(sum(lens))
     dfa = acg.build(w.patterns)
     packed = [acg.pack(t.contiguous()) for t in w.texts]
-    whole = acg.pack(torch.cat([t for t in w.texts]))  # the batch as one text: the tuner's sample
-    acg.autotune(dfa, whole, total)
+    whole = acg.pack(torch.cat([t for t in w.texts]))  # the batch as one text: the tuner's sample for the shape
+    tuned = acg.autotune(dfa, whole, total)
+    tuned_chunk = acg.autotune_batch(dfa, packed, lens)  # the work-item chunk, on the batch itself
     del w.texts, whole
     sp = torch.cuda.current_stream().cuda_stream
     # size outputs
@@ -607,37 +643,79 @@ def run_batched(args, steps: int):
         lib.ac_scan_batch(dfa.h, descs, len(packed), ctypes.byref(r), None, sp, ctypes.byref(stt))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kern = []
+    kern, bwalk = [], 0
     for _ in range(steps):
         assert lib.ac_scan_batch(dfa.h, descs, len(packed), ctypes.byref(r), None, sp, ctypes.byref(stt)) == 0
         kern.append(stt.scan_ms)
+        bwalk = stt.bases_walked
     batch_call_ms = (time.perf_counter() - t0) * 1e3 / steps
-    # the plain per-text loop: one ac_scan per text
+    batch_shape = {k: getattr(stt, k) for k in ("stride", "chunk", "threads", "interleave", "hot_states", "grid")}
+    # the plain per-text loop: one ac_scan per text, each with its own event-timed device time
     single = [(N.Text(p.data_ptr(), n, N.AC_TEXT_PACKED2, 1)) for p, n in zip(packed, lens)]
     loop_passes = max(1, min(steps, 3))
+    loop_dev, loop_kern = [], []
+    st1 = N.ScanStats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     occ_loop = 0
     for _ in range(loop_passes):
-        occ_loop = 0
+        occ_loop, dev_ms, kern_ms = 0, 0.0, 0.0
         for i, d in enumerate(single):
             rr = N.Result(raw.data_ptr(), cap, 0, cnt.data_ptr(), 1, 0, 0)
             o = N.ScanOpts()
             o.hot_states = -1
             o.text_id = i
-            assert lib.ac_scan(dfa.h, ctypes.byref(d), ctypes.byref(rr), ctypes.byref(o), sp, None) == 0
+            assert lib.ac_scan(dfa.h, ctypes.byref(d), ctypes.byref(rr), ctypes.byref(o), sp, ctypes.byref(st1)) == 0
             occ_loop += rr.n_matches
+            dev_ms += st1.total_ms
+            kern_ms += st1.scan_ms
+        loop_dev.append(dev_ms)
+        loop_kern.append(kern_ms)
     loop_ms = (time.perf_counter() - t0) * 1e3 / loop_passes
     assert occ_loop == n_occ
     plan.close()
+    loop_dev_ms, loop_kern_ms = float(np.median(loop_dev)), float(np.median(loop_kern))
+    # walk-only ceiling of the batch kernel: the same texts and shape, 50,000 uniform keywords (no occurrences)
+    uni = acg.build(synth.uniform_patterns(len(w.patterns), 15, 25, synth.BASE_SEED + 79))
+    o_u = N.ScanOpts()
+    o_u.hot_states, o_u.chunk = -1, batch_shape["chunk"]
+    ru = N.Result(raw.data_ptr(), cap, 0, None, 1, 0, 0)
+    su = N.ScanStats()
+    uk = []
+    for i in range(4):
+        rc = lib.ac_scan_batch(uni.h, descs, len(packed), ctypes.byref(ru), ctypes.byref(o_u), sp, ctypes.byref(su))
+        assert rc in (0, N.AC_ERR_OVERFLOW), rc
+        if i:
+            uk.append(su.scan_ms)
+    uni.close()
+    peak, peak_kind = load_peaks()
+    bk = float(np.mean(kern))
+    alg = total / 4 + 16 * n_occ
     return {
         "workload": w.name, "texts": len(lens), "bases": total, "occurrences": n_occ,
-        "states": dfa.info["n_states"],
+        "states": dfa.info["n_states"], "tuned": {**tuned, "batch_chunk": tuned_chunk}, "shape": batch_shape,
         "graph_replay_gbases_s": round(total / (graph_ms / 1e3) / 1e9, 3), "graph_replay_ms": round(graph_ms, 4),
         "batch_call_gbases_s": round(total / (batch_call_ms / 1e3) / 1e9, 3),
-        "batch_kernel_ms": round(float(np.mean(kern)), 4),
-        "per_text_loop_gbases_s": round(total / (loop_ms / 1e3) / 1e9, 3), "per_text_loop_ms": round(loop_ms, 2),
-        "batched_over_loop": round(loop_ms / graph_ms, 2),
+        "batch_call_wall_ms": round(batch_call_ms, 4),
+        "batch_kernel_ms": round(bk, 4),
+        "per_text_loop": {
+            "device_ms": round(loop_dev_ms, 3), "device_gbases_s": round(total / (loop_dev_ms / 1e3) / 1e9, 3),
+            "kernels_ms": round(loop_kern_ms, 3), "kernels_gbases_s": round(total / (loop_kern_ms / 1e3) / 1e9, 3),
+            "wall_ms": round(loop_ms, 2), "wall_gbases_s": round(total / (loop_ms / 1e3) / 1e9, 3),
+            "calls": len(single)},
+        # ratios on one clock each
+        "batched_over_loop_device": round(loop_dev_ms / graph_ms, 2),  # events: loop calls' device time vs replay
+        "batch_kernel_over_loop_kernels": round(loop_kern_ms / bk, 2),  # events: scan kernels only
+        "batched_over_loop_wall": round(loop_ms / batch_call_ms, 2),  # host wall: ac_scan loop vs ac_scan_batch
+        "roofline": {"bound": "hbm", "kernel": "batch_kernel", "kernel_ms": round(bk, 4),
+                     "algorithmic_bytes": int(alg), "achieved": round(alg / (bk / 1e3) / 1e9, 2), "peak": peak,
+                     "unit": "GB/s", "frac": round(alg / (bk / 1e3) / 1e9 / peak, 5), "peak_source": peak_kind,
+                     "walked_bases_per_s": round(bwalk / (bk / 1e3), 1),
+                     "lookup": {"ceiling_kernel_ms": round(float(np.median(uk)), 4),
+                                "ceiling_walked_bases_per_s": round(su.bases_walked / (float(np.median(uk)) / 1e3), 1),
+                                "frac": round(float(np.median(uk)) / bk, 4),
+                                "ceiling_source": "same texts, shape and chunk, 50,000 uniform keywords of 15-25 "
+                                                  "(no occurrences)"}},
     }
 
 
@@ -1042,7 +1120,7 @@ def main():
             out["cpu_baseline"] = {"value": None, "error": repr(e)}
         if args.workload == "genome" and world == 1:
             out["batched"] = run_batched(args, max(3, args.steps))
-            out["serving"] = run_serving(args, args.serve_seconds or 5.0, 1.0)
+            out["serving"] = run_serving(args, args.serve_seconds or 60.0, 5.0)
             out["plain_configs"] = run_plain_configs(args, world, rank, local)
     if rank == 0:
         print(json.dumps(out), flush=True)

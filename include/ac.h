@@ -225,7 +225,9 @@ typedef struct {
     uint32_t text_id;     /* copied into every ac_match.text_id (ac_scan only)  */
     uint32_t stride;      /* bases per table lookup: 1, 2 (needs the two-base
                              table), 3 (needs the three-base table), or 0 = tuned */
-    uint32_t reserved;
+    uint32_t chunks_per_lane; /* when chunk is 0: the owned range is cut into
+                             this many chunks per resident lane (1, 2, 4 or 8);
+                             0 = tuned (1 when untuned)                         */
 } ac_scan_opts;
 
 /* Timing and launch shape of the last scan, filled when requested. */
@@ -236,7 +238,8 @@ typedef struct {
     float counts_ms;     /* device time of the count kernel                        */
     uint32_t chunk, threads, interleave, hot_states, grid, blocks_per_sm;
     uint32_t stride;       /* bases per lookup used                                */
-    uint32_t reserved;
+    uint32_t chunks_per_lane; /* chunks per resident lane the chunk length came from
+                                 (0 when the chunk was given or fixed by a batch)  */
     uint64_t bases_walked; /* owned bases plus halo re-reads                       */
 } ac_scan_stats;
 
@@ -409,12 +412,28 @@ int ac_batch_plan_run(ac_batch_plan* plan, void* stream, int sync, ac_result* re
 void ac_batch_plan_free(ac_batch_plan* plan);
 
 /* ---------------------------------------------------------------- autotune
- * Times candidate launch shapes (chunk, threads, interleave, shared-memory
- * states) on a sample of a device-resident packed text and returns the
- * fastest in *best. Results are cached per (device, dfa size class, text
- * size class) for the life of the process; AC_TUNE=off skips the trials
- * and returns the built-in defaults. */
+ * Times candidate launch shapes (bases per lookup, threads, interleave,
+ * shared-memory states, then chunks per lane for the best of those) on a
+ * device-resident packed text and returns the fastest in *best (best->chunk
+ * = the chunk length it gives for this text). Every trial writes all of its
+ * occurrences. Results are cached per (device, dfa size class, text size
+ * class), where a size class is ceil(log2(x)), for the life of the process
+ * (and in the file AC_TUNE_CACHE names, if set); later scans whose classes
+ * match use the tuned shape unless the caller fixes one. AC_TUNE=off skips
+ * the trials and returns the built-in defaults. */
 int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opts* best, void* stream);
+
+/* Tunes the chunk length of batched scans (ac_scan_batch, batch plans): the
+ * work-stealing grain, in bases of one text per work item. Times
+ * ac_scan_batch over texts (device-resident AC_TEXT_PACKED2) with candidate
+ * chunks from the keyword halo rounded up to 64 bases up to 32 times that,
+ * and the built-in default, in the launch shape ac_scan would use for the
+ * batch's total length. Cached per (device, dfa size class, class of the
+ * total bases); later batches whose classes match use the tuned chunk unless
+ * opts->chunk is set. best->chunk is the chosen chunk. Errors as
+ * ac_scan_batch. */
+int ac_autotune_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_scan_opts* best,
+                      void* stream);
 
 /* ----------------------------------------------------------------- serving
  * Continuous batching over several resident dfas. Requests (host texts) are

@@ -24,7 +24,7 @@ from ._native import AcError
 
 __all__ = [
     "Dfa", "ScanResult", "build", "pack", "scan", "scan_failureless", "scan_batch", "BatchPlan", "Stream", "PartSet",
-    "build_partitioned", "autotune", "Server", "fault_inject", "mem_usage",
+    "build_partitioned", "autotune", "autotune_batch", "Server", "fault_inject", "mem_usage",
     "AcError", "lib",
 ]
 
@@ -187,11 +187,13 @@ def _split(raw: torch.Tensor, k: int):
     return pos, pid, tid
 
 
-def _opts(range_=None, chunk=0, threads=0, interleave=0, hot_states=-1, fold_case=False, text_id=0, stride=0):
+def _opts(range_=None, chunk=0, threads=0, interleave=0, hot_states=-1, fold_case=False, text_id=0, stride=0,
+          chunks_per_lane=0):
     o = N.ScanOpts()
     o.range_begin, o.range_end = (range_ if range_ is not None else (0, 0))
     o.chunk, o.threads, o.interleave, o.hot_states = chunk, threads, interleave, hot_states
     o.stride = stride
+    o.chunks_per_lane = chunks_per_lane
     o.flags = N.AC_SCAN_FOLD_CASE if fold_case else 0
     o.text_id = text_id
     return o
@@ -230,14 +232,15 @@ def _run(fn, dfa, texts_arg, n_texts, capacity, counts, device, opts, stream, wa
 def scan(dfa: Dfa, text, *, encoding: int | None = None, n_bases: int | None = None, capacity: int | None = None,
          counts: bool = True, range_=None, chunk: int = 0, threads: int = 0, interleave: int = 0,
          hot_states: int = -1, fold_case: bool = False, text_id: int = 0, stats: bool = False,
-         stream=None, results_on_device: bool | None = None, stride: int = 0) -> ScanResult:
+         stream=None, results_on_device: bool | None = None, stride: int = 0,
+         chunks_per_lane: int = 0) -> ScanResult:
     """One text (ac_scan). text: uint8 ASCII or int32 packed (give n_bases), on CUDA or host."""
     desc, keep = _text_desc(text, encoding, n_bases)
     on_dev = bool(desc.on_device) if results_on_device is None else results_on_device
     device = text.device if isinstance(text, torch.Tensor) and text.is_cuda else torch.device("cuda")
     if capacity is None:
         capacity = max(1024, desc.n_bases // 64)
-    o = _opts(range_, chunk, threads, interleave, hot_states, fold_case, text_id, stride)
+    o = _opts(range_, chunk, threads, interleave, hot_states, fold_case, text_id, stride, chunks_per_lane)
     res = _run(lib().ac_scan, dfa, ctypes.byref(desc), None, capacity, counts, device, o, _stream_ptr(stream),
                stats, on_dev)
     del keep
@@ -426,10 +429,23 @@ class Stream:
 
 
 def autotune(dfa: Dfa, packed_sample: torch.Tensor, n_bases: int, stream=None) -> dict:
+    """Tunes the scan's launch shape on a device-resident packed text (ac_autotune)."""
     desc = N.Text(packed_sample.data_ptr(), int(n_bases), N.AC_TEXT_PACKED2, 1)
     o = N.ScanOpts()
     N.check(lib().ac_autotune(dfa.h, ctypes.byref(desc), ctypes.byref(o), _stream_ptr(stream)), "ac_autotune")
-    return {"threads": o.threads, "interleave": o.interleave, "hot_states": o.hot_states, "stride": o.stride}
+    return {"threads": o.threads, "interleave": o.interleave, "hot_states": o.hot_states, "stride": o.stride,
+            "chunks_per_lane": o.chunks_per_lane, "chunk": o.chunk}
+
+
+def autotune_batch(dfa: Dfa, packed_texts: Sequence[torch.Tensor], n_bases: Sequence[int], stream=None) -> int:
+    """Tunes the work-item chunk of batched scans over device-resident packed texts
+    (ac_autotune_batch); returns the chosen chunk (0: the built-in default)."""
+    descs = [N.Text(t.data_ptr() if n else None, int(n), N.AC_TEXT_PACKED2, 1) for t, n in zip(packed_texts, n_bases)]
+    arr = (N.Text * max(1, len(descs)))(*descs)
+    o = N.ScanOpts()
+    N.check(lib().ac_autotune_batch(dfa.h, arr, len(descs), ctypes.byref(o), _stream_ptr(stream)),
+            "ac_autotune_batch")
+    return int(o.chunk)
 
 
 def fault_inject(spec: str | None) -> None:

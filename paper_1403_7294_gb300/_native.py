@@ -76,7 +76,7 @@ class ScanOpts(ctypes.Structure):
     _fields_ = [
         ("range_begin", u64), ("range_end", u64), ("chunk", u32), ("threads", u32),
         ("interleave", u32), ("hot_states", i32), ("flags", u32), ("text_id", u32), ("stride", u32),
-        ("reserved", u32),
+        ("chunks_per_lane", u32),
     ]
 
 
@@ -84,7 +84,7 @@ class ScanStats(ctypes.Structure):
     _fields_ = [
         ("total_ms", ctypes.c_float), ("scan_ms", ctypes.c_float), ("pack_ms", ctypes.c_float),
         ("counts_ms", ctypes.c_float), ("chunk", u32), ("threads", u32), ("interleave", u32),
-        ("hot_states", u32), ("grid", u32), ("blocks_per_sm", u32), ("stride", u32), ("reserved", u32),
+        ("hot_states", u32), ("grid", u32), ("blocks_per_sm", u32), ("stride", u32), ("chunks_per_lane", u32),
         ("bases_walked", u64),
     ]
 
@@ -146,6 +146,7 @@ SIGNATURES = {
     "ac_batch_plan_run": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.POINTER(Result)]),
     "ac_batch_plan_free": (None, [P]),
     "ac_autotune": (ctypes.c_int, [P, ctypes.POINTER(Text), ctypes.POINTER(ScanOpts), P]),
+    "ac_autotune_batch": (ctypes.c_int, [P, ctypes.POINTER(Text), u32, ctypes.POINTER(ScanOpts), P]),
     "ac_serve_create": (ctypes.c_int, [ctypes.POINTER(ServeOpts), ctypes.POINTER(P)]),
     "ac_serve_add_dfa": (ctypes.c_int, [P, P, ctypes.POINTER(u32)]),
     "ac_serve_submit": (ctypes.c_int, [P, u32, ctypes.POINTER(Text), ctypes.POINTER(u64)]),

@@ -413,6 +413,15 @@ extern "C" int ac_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, uint3
 
 // ----------------------------------------------------------------- shapes
 
+uint32_t ac_chunk_for(uint64_t owned, uint64_t lanes, uint32_t cpl, uint32_t halo) {
+    const uint64_t per = std::max<uint64_t>(lanes, 1) * std::max<uint32_t>(cpl, 1);
+    uint64_t c = (owned + per - 1) / per;
+    // short texts: at least 64 owned bases per chunk (walk latency, not halo
+    // re-reads, is what a short text costs)
+    c = std::max<uint64_t>(c, std::max<uint64_t>(64, round_up(halo, 64)));
+    return (uint32_t)std::min<uint64_t>(c, 1u << 30);
+}
+
 ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts* o) {
     const DeviceProps& p = ac_device_props();
     const HostTables& h = dfa->host;
@@ -429,6 +438,7 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     if (o && o->interleave) sh.interleave = o->interleave;
     if (o && o->stride) sh.stride = o->stride;
     if (o && o->hot_states >= 0) sh.hot = (uint32_t)o->hot_states;
+    if (o && o->chunks_per_lane) sh.cpl = o->chunks_per_lane;
     if (o && o->chunk) sh.chunk = o->chunk;
     // built-in default (measured best on the benchmark workloads when untuned):
     // one chain per thread, 1024 threads, half of the shared memory for states
@@ -447,12 +457,10 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
     const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
     if (!sh.chunk) {
-        const uint64_t halo = h.max_len ? h.max_len - 1 : 0;
-        uint64_t c = (owned + lanes - 1) / std::max<uint64_t>(lanes, 1);  // one chunk per lane
-        // short texts: at least 64 owned bases per chunk (walk latency, not halo
-        // re-reads, is what a short text costs)
-        c = std::max<uint64_t>(c, std::max<uint64_t>(64, round_up(halo, 64)));
-        sh.chunk = (uint32_t)std::min<uint64_t>(c, 1u << 30);
+        if (!sh.cpl) sh.cpl = 1;  // one chunk per lane unless tuned or asked otherwise
+        sh.chunk = ac_chunk_for(owned, lanes, sh.cpl, h.max_len ? h.max_len - 1 : 0);
+    } else if (o && o->chunk) {
+        sh.cpl = 0;  // the caller's chunk
     }
     const uint64_t n_chunks = (owned + sh.chunk - 1) / sh.chunk;
     const uint64_t per_block = (uint64_t)sh.threads * sh.interleave;
@@ -468,6 +476,9 @@ bool ac_valid_shape_opts(const ac_scan_opts* o) {
         return false;
     if (o->threads && o->threads > ac_max_threads(o->interleave ? o->interleave : 1)) return false;
     if (o->stride > 3 || (o->stride == 2 && o->interleave == 8) || (o->stride == 3 && o->interleave > 2)) return false;
+    if (o->chunks_per_lane && o->chunks_per_lane != 1 && o->chunks_per_lane != 2 && o->chunks_per_lane != 4 &&
+        o->chunks_per_lane != 8)
+        return false;
     return true;
 }
 
@@ -577,6 +588,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
             stats->grid = 0;
             stats->blocks_per_sm = 0;
             stats->stride = 1;
+            stats->chunks_per_lane = 0;
             stats->bases_walked = own_end - own_begin;
         }
         return status;
@@ -628,6 +640,7 @@ int scan_core(const ac_dfa* dfa, const uint32_t* words, uint64_t n, uint64_t own
         stats->grid = sh.grid;
         stats->blocks_per_sm = sh.blocks_per_sm;
         stats->stride = sh.stride;
+        stats->chunks_per_lane = sh.cpl;
         const uint64_t owned = own_end - own_begin;
         const uint64_t n_chunks = owned ? (owned + sh.chunk - 1) / sh.chunk : 0;
         stats->bases_walked = owned + n_chunks * (uint64_t)(h.max_len - 1);
@@ -844,10 +857,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
         // ---- scan the owned piece
         ScanShape sh = full;  // shape of the whole range; chunks re-sized to the piece unless given
         const uint64_t len = b - a;
-        if (!(opts && opts->chunk))
-            sh.chunk = (uint32_t)std::min<uint64_t>(std::max<uint64_t>((len + lanes - 1) / std::max<uint64_t>(lanes, 1),
-                                                                       std::max<uint64_t>(64, round_up(halo, 64))),
-                                                    1u << 30);
+        if (!(opts && opts->chunk)) sh.chunk = ac_chunk_for(len, lanes, full.cpl, (uint32_t)halo);
         const uint64_t nch = (len + sh.chunk - 1) / sh.chunk;
         sh.grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (nch + (uint64_t)sh.threads * sh.interleave - 1) /
                                                                       ((uint64_t)sh.threads * sh.interleave)),
@@ -1284,6 +1294,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
         stats->grid = gx * k;
         stats->blocks_per_sm = 1;
         stats->stride = 1;
+        stats->chunks_per_lane = 0;
         const uint64_t n_chunks = owned ? (owned + chunk - 1) / chunk : 0;
         stats->bases_walked = (uint64_t)k * (owned + n_chunks * set->halo);
     }
@@ -1303,8 +1314,12 @@ struct BatchLayout {
 ScanShape batch_shape(const ac_dfa* dfa, uint64_t total, const ac_scan_opts* opts, uint32_t n_texts) {
     ScanShape sh = ac_default_shape(dfa, total, opts);
     const DeviceProps& p = ac_device_props();
-    if (!(opts && opts->chunk)) {
-        // enough chunks for every lane of the wave, at least 256 bases each
+    sh.cpl = 0;
+    uint32_t tuned = 0;
+    if (!(opts && opts->chunk) && ac_tuned_batch_chunk(dfa, total, &tuned)) {
+        sh.chunk = tuned;
+    } else if (!(opts && opts->chunk)) {
+        // built-in default: enough chunks for every lane of the wave, at least 256 bases each
         const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
         const uint64_t halo = dfa->host.max_len ? dfa->host.max_len - 1 : 0;
         uint64_t c = round_up(std::max<uint64_t>(1, total / std::max<uint64_t>(lanes, 1)), 64);
@@ -1470,6 +1485,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
         stats->grid = sh.grid;
         stats->blocks_per_sm = sh.blocks_per_sm;
         stats->stride = sh.stride;
+        stats->chunks_per_lane = 0;
         stats->bases_walked = total + prefix.back() * (uint64_t)(h.max_len - 1);
     }
     return status;

@@ -85,6 +85,7 @@ struct ScanShape {
     uint32_t hot = 0;         // states in shared memory
     uint32_t grid = 0;        // blocks
     uint32_t blocks_per_sm = 0;
+    uint32_t cpl = 0;         // chunks per resident lane the chunk came from (0: given or fixed)
 };
 
 struct DeviceProps {
@@ -244,3 +245,8 @@ bool ac_stride_tables_present(const ac_dfa* dfa, const ac_scan_opts* o);
 // Default / tuned shape selection (ac_api.cu / ac_tune.cpp)
 ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned_bases, const ac_scan_opts* opts);
 bool ac_tuned_lookup(const ac_dfa* dfa, uint64_t n, ScanShape* out);
+// The chunk tuned for batches of this dfa size and total length, if any.
+bool ac_tuned_batch_chunk(const ac_dfa* dfa, uint64_t total, uint32_t* chunk);
+// Chunk length for `owned` bases cut into `cpl` chunks per lane over `lanes`
+// lanes: at least 64 bases and at least the halo rounded up to 64.
+uint32_t ac_chunk_for(uint64_t owned, uint64_t lanes, uint32_t cpl, uint32_t halo);

@@ -336,3 +336,29 @@ def test_serve_wait_timeout_keeps_ticket():
     m, c, k = srv.wait(tk, slot, capacity=1000)
     assert k == 1000
     srv.close()
+
+
+def test_batch_chunk_candidates_and_tuner_are_exact():
+    """Every work-item chunk the batch tuner tries (the halo rounded up to 64 bases, times 1 .. 32,
+    and the built-in default) gives the oracle's result; the tuned chunk is then used by default."""
+    texts, pats = batch_case(14, 120)
+    d = acg.build(pats)
+    want, counts = oracle_batch(pats, texts)
+    pk = packed_dev(texts)
+    lens = [len(t) for t in texts]
+    unit = max(64, (max(len(p) for p in pats) - 1 + 63) // 64 * 64)
+    for chunk in [0] + [unit * m for m in (1, 2, 4, 8, 16, 32)]:
+        r = acg.scan_batch(d, pk, encoding=N.AC_TEXT_PACKED2, n_bases=lens, capacity=16, chunk=chunk, stats=True)
+        assert np.array_equal(r.canonical(), want), chunk
+        assert r.counts.cpu().numpy().tolist() == counts.tolist()
+        if chunk:
+            assert r.stats["chunk"] == chunk
+    tuned = acg.autotune_batch(d, pk, lens)
+    assert tuned in [unit * m for m in (1, 2, 4, 8, 16, 32)] or tuned >= 64
+    r = acg.scan_batch(d, pk, encoding=N.AC_TEXT_PACKED2, n_bases=lens, stats=True)
+    assert r.stats["chunk"] == tuned
+    assert np.array_equal(r.canonical(), want)
+    plan = acg.BatchPlan(d, pk, lens, capacity=len(want) + 10)  # plans take the tuned chunk too
+    assert plan.run() == len(want)
+    assert np.array_equal(plan.result().canonical(), want)
+    plan.close()

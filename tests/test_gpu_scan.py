@@ -259,3 +259,31 @@ def test_autotune_then_exact():
     r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), threads=best["threads"],
                  interleave=best["interleave"], hot_states=best["hot_states"])
     assert_same(r, want, counts)
+
+
+@pytest.mark.parametrize("stride,threads", [(1, 0), (2, 0), (3, 0), (3, 640)])
+def test_every_tuner_chunk_candidate_is_exact(stride, threads):
+    """The tuner's chunk axis: 1, 2, 4 and 8 chunks per resident lane (shorter chunks, more halo
+    re-reads) give the oracle's occurrences and counts on the fuzz set."""
+    for pats, text in _cases(78, 12):
+        d = acg.build(pats)
+        want, counts = oracle_canonical(pats, text)
+        for cpl in (1, 2, 4, 8):
+            r = acg.scan(d, to_dev(text), capacity=4, stride=stride, threads=threads, chunks_per_lane=cpl,
+                         stats=True)
+            assert_same(r, want, counts)
+            assert r.stats["chunks_per_lane"] == cpl
+
+
+def test_autotune_picks_a_chunk_and_stays_exact():
+    rng = random.Random(19)
+    text = rand_dna(rng, 4 << 20) + b"ACGT" * 5000
+    pats = [text[j : j + rng.randint(12, 24)] for j in rng.sample(range((4 << 20) - 30), 4000)]
+    d = acg.build(pats)
+    packed = acg.pack(to_dev(text))
+    best = acg.autotune(d, packed, len(text))
+    assert best["chunks_per_lane"] in (1, 2, 4, 8) and best["chunk"] > 0
+    want, counts = oracle_canonical(pats, text)
+    r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), stats=True)  # the tuned shape
+    assert_same(r, want, counts)
+    assert (r.stats["chunks_per_lane"], r.stats["chunk"]) == (best["chunks_per_lane"], best["chunk"])
