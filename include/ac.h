@@ -463,6 +463,7 @@ typedef struct {
     double gbases_per_s;                    /* bases_completed / busy_s / 1e9  */
     uint64_t overflow_batches;              /* batches that outgrew their output reservation
                                                and ran once more with the exact room        */
+    uint64_t cancelled;                     /* requests cancelled before they ran           */
 } ac_serve_stats_t;
 
 int ac_serve_create(const ac_serve_opts* opts /* nullable */, ac_server** out);
@@ -497,6 +498,13 @@ typedef struct {
 int ac_serve_take(ac_server* srv, uint64_t ticket, ac_served* out, int64_t timeout_us);
 /* Gives back the memory of one ac_serve_take result (null: no-op). */
 void ac_serve_release(void* handle);
+/* Withdraws a request. One still waiting in the queue is removed and never
+ * scanned, and its ticket is forgotten (AC_OK; it counts as cancelled). A
+ * finished one that was not yet waited for has its results dropped and its
+ * ticket forgotten (AC_OK). One whose batch is running on the device cannot be
+ * withdrawn: AC_ERR_BUSY (the ticket stays valid; wait for it or cancel again
+ * once it is done). AC_ERR_NOT_FOUND for an unknown ticket. */
+int ac_serve_cancel(ac_server* srv, uint64_t ticket);
 int ac_serve_stats(ac_server* srv, ac_serve_stats_t* out);
 /* Finishes in-flight work, then frees everything. */
 void ac_serve_destroy(ac_server* srv);

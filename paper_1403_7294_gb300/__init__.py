@@ -557,6 +557,15 @@ class Server:
             return raw[:k], cnt, k
         raise AssertionError("unreachable")
 
+    def cancel(self, ticket: int) -> bool:
+        """Withdraws a request (ac_serve_cancel): True when it was still queued, or finished and its
+        results are dropped; False when its batch is running (the ticket stays valid)."""
+        st = lib().ac_serve_cancel(self.h, ticket)
+        if st == N.AC_ERR_BUSY:
+            return False
+        N.check(st, "ac_serve_cancel")
+        return True
+
     def stats(self) -> dict:
         s = N.ServeStats()
         N.check(lib().ac_serve_stats(self.h, ctypes.byref(s)), "ac_serve_stats")

@@ -106,6 +106,7 @@ class ServeStats(ctypes.Structure):
         ("bases_completed", u64), ("batches_launched", u64), ("p50_ms", ctypes.c_double),
         ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
         ("busy_s", ctypes.c_double), ("gbases_per_s", ctypes.c_double), ("overflow_batches", u64),
+        ("cancelled", u64),
     ]
 
 
@@ -153,6 +154,7 @@ SIGNATURES = {
     "ac_serve_wait": (ctypes.c_int, [P, u64, ctypes.POINTER(Result), i64]),
     "ac_serve_take": (ctypes.c_int, [P, u64, ctypes.POINTER(Served), i64]),
     "ac_serve_release": (None, [P]),
+    "ac_serve_cancel": (ctypes.c_int, [P, u64]),
     "ac_serve_stats": (ctypes.c_int, [P, ctypes.POINTER(ServeStats)]),
     "ac_serve_destroy": (None, [P]),
     "ac_fault_inject": (ctypes.c_int, [ctypes.c_char_p]),

@@ -208,6 +208,7 @@ struct ac_server {
     // stats
     uint64_t submitted = 0, completed = 0, rejected = 0, failed = 0, bases_completed = 0, batches = 0;
     uint64_t overflow_batches = 0;  // batches run twice for want of output room
+    uint64_t cancelled = 0;         // requests withdrawn before they ran
     std::vector<double> lat_ms;
     double busy_s = 0.0;
     Clock::time_point busy_since;
@@ -665,6 +666,28 @@ extern "C" int ac_serve_take(ac_server* s, uint64_t ticket, ac_served* out, int6
 
 extern "C" void ac_serve_release(void* handle) { delete static_cast<Taken*>(handle); }
 
+extern "C" int ac_serve_cancel(ac_server* s, uint64_t ticket) {
+    if (!s) return AC_ERR_INVALID_ARG;
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->by_ticket.find(ticket);
+        if (it == s->by_ticket.end()) return AC_ERR_NOT_FOUND;
+        r = it->second;
+        if (r->done) {  // finished, not yet waited for: drop its results
+            s->by_ticket.erase(it);
+            return AC_OK;
+        }
+        auto q = std::find(s->pending.begin(), s->pending.end(), r);
+        if (q == s->pending.end()) return AC_ERR_BUSY;  // its batch is on the device
+        s->pending.erase(q);
+        s->by_ticket.erase(it);
+        s->cancelled++;
+    }
+    s->cv_work.notify_all();  // the queue changed: a worker may now admit the next request
+    return AC_OK;  // r (and its text) goes when the last reference does
+}
+
 extern "C" int ac_serve_stats(ac_server* s, ac_serve_stats_t* o) {
     if (!s || !o) return AC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -676,6 +699,7 @@ extern "C" int ac_serve_stats(ac_server* s, ac_serve_stats_t* o) {
     o->bases_completed = s->bases_completed;
     o->batches_launched = s->batches;
     o->overflow_batches = s->overflow_batches;
+    o->cancelled = s->cancelled;
     double busy = s->busy_s;
     if (s->active_batches) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
     o->busy_s = busy;

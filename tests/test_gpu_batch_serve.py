@@ -362,3 +362,49 @@ def test_batch_chunk_candidates_and_tuner_are_exact():
     assert plan.run() == len(want)
     assert np.array_equal(plan.result().canonical(), want)
     plan.close()
+
+
+def test_serve_cancel():
+    """A request still queued behind a running batch is withdrawn and never scanned; a finished one
+    that was not waited for has its results dropped; an unknown ticket is not found; a request whose
+    batch is on the device cannot be withdrawn and stays waitable. The server goes on serving."""
+    rng = random.Random(33)
+    small = rand_dna(rng, 5000) + b"ACGTACGT"
+    pats = [small[j : j + 10] for j in rng.sample(range(4900), 50)] + [b"ACGTACGT"]
+    d_a, d_b = acg.build([b"ACGTACGTAC", b"GGGGG"]), acg.build(pats)
+    srv = acg.Server(n_streams=1, max_batch=4)  # one worker: while it scans A, B waits in the queue
+    sa, sb = srv.add_dfa(d_a), srv.add_dfa(d_b)  # different machines: A and B are never batched together
+    big = np.frombuffer(rand_dna(rng, 1 << 20) * 128, np.uint8)  # 128 Mbase
+    k_big = acg.scan(d_a, torch.tensor(big, device=DEV)).n_matches
+    ta = srv.submit(sa, big)
+    tb = srv.submit(sb, small)
+    assert srv.cancel(tb)
+    with pytest.raises(acg.AcError) as e:
+        srv.wait(tb, sb)
+    assert e.value.status == N.AC_ERR_NOT_FOUND
+    assert srv.wait(ta, sa)[2] == k_big
+    want, counts = oracle_canonical(pats, small)
+    tc = srv.submit(sb, small)
+    m, c, k = srv.wait(tc, sb)
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and np.array_equal(c, counts)
+    done_before = srv.stats()["completed"]
+    td = srv.submit(sb, small)
+    t0 = time.time()
+    while srv.stats()["completed"] == done_before:  # finished, not waited for
+        assert time.time() - t0 < 30
+        time.sleep(0.001)
+    assert srv.cancel(td)
+    with pytest.raises(acg.AcError):
+        srv.wait(td, sb)
+    with pytest.raises(acg.AcError) as e:
+        srv.cancel(987654321)
+    assert e.value.status == N.AC_ERR_NOT_FOUND
+    te = srv.submit(sa, big)
+    t0 = time.time()
+    while srv.stats()["batches_launched"] < 4:  # batches of A, C, D, then E's
+        assert time.time() - t0 < 30
+    if not srv.cancel(te):  # its batch is on the device: not withdrawn, and its result still comes
+        assert srv.wait(te, sa)[2] == k_big
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["failed"] == 0
+    srv.close()
