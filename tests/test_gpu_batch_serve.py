@@ -408,3 +408,37 @@ def test_serve_cancel():
     st = srv.stats()
     assert st["cancelled"] == 1 and st["failed"] == 0
     srv.close()
+
+
+def test_serve_split_batch_results_taken_without_copy():
+    """Requests split out of one multi-request batch share one pinned block: each taken result
+    (views, no copy) equals the oracle's, and stays valid while the batch's other results are
+    released, and after the server is gone."""
+    rng = random.Random(34)
+    genome = rand_dna(rng, 300_000)
+    pats = [genome[j : j + rng.randint(8, 14)] for j in rng.sample(range(299_000), 400)] + [b"ACGTAC"]
+    d = acg.build(pats)
+    srv = acg.Server(n_streams=1, max_batch=32)
+    slot = srv.add_dfa(d)
+    big = np.frombuffer(rand_dna(rng, 1 << 20) * 64, np.uint8)  # keeps the one worker busy meanwhile
+    d_big = acg.build([b"ACGTACGTAC"])
+    s_big = srv.add_dfa(d_big)
+    t_big = srv.submit(s_big, big)
+    texts = [genome[o : o + n] for o, n in ((rng.randint(0, 250_000), rng.randint(0, 40_000)) for _ in range(20))]
+    tickets = [srv.submit(slot, t) for t in texts]  # queued together: one batch behind the big one
+    got = [srv.wait(tk, slot) for tk in tickets]
+    srv.wait(t_big, s_big)
+    st = srv.stats()
+    assert st["batches_launched"] < 1 + len(texts)  # the 20 requests were batched together
+    wants = [oracle_canonical(pats, t) for t in texts]
+    for i in rng.sample(range(len(texts)), len(texts)):  # release in random order, check the rest
+        m, c, k = got[i]
+        want, counts = wants[i]
+        assert k == len(want)
+        assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and np.array_equal(c, counts)
+        got[i] = None
+        del m, c
+    keep = srv.wait(srv.submit(slot, texts[3]), slot)
+    srv.close()
+    m, c, k = keep
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], wants[3][0][:, 1:]) and np.array_equal(c, wants[3][1])
