@@ -196,7 +196,10 @@ typedef struct {
 } ac_match;              /* 16 bytes */
 
 typedef struct {
-    ac_match* matches;   /* capacity entries, or NULL with capacity 0 (counts only) */
+    ac_match* matches;   /* capacity entries, or NULL with capacity 0 (counts only);
+                            in device memory it must be 16-byte aligned (else
+                            AC_ERR_INVALID_ARG): occurrences are written as whole
+                            16-byte records                                         */
     uint64_t capacity;   /* entries available at matches                            */
     uint64_t n_matches;  /* out: exact number of occurrences (also on overflow)      */
     uint64_t* counts;    /* [n_patterns] out: occurrences per keyword, or NULL       */

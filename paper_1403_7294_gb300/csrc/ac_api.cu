@@ -693,6 +693,7 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
     if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
     if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
         return AC_ERR_INVALID_ARG;
@@ -960,6 +961,7 @@ extern "C" int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_re
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
     if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
         return AC_ERR_INVALID_ARG;
     const uint64_t n = text->n_bases;
@@ -1045,6 +1047,7 @@ extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, 
     if (piece->n_bases && !piece->data) return AC_ERR_INVALID_ARG;
     if (piece->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
     if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
         return AC_ERR_INVALID_ARG;
@@ -1197,6 +1200,7 @@ extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, 
     if (text->n_bases && !text->data) return AC_ERR_INVALID_ARG;
     if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (text->on_device && text->encoding == AC_TEXT_PACKED2 && (reinterpret_cast<uintptr_t>(text->data) & 15))
         return AC_ERR_INVALID_ARG;
     const uint64_t n = text->n_bases;
@@ -1345,6 +1349,7 @@ extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n
     r->bad_offset = ~0ull;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
     if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
         return AC_ERR_INVALID_ARG;
@@ -1525,6 +1530,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     if (!dfa || !r || !out || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (!r->on_device || (r->capacity && !r->matches)) return AC_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(r->matches) & 15) return AC_ERR_INVALID_ARG;  // 16-byte records
     if (!valid_shape_opts(opts)) return AC_ERR_INVALID_ARG;
     if (opts && ((opts->stride == 2 && !dfa->d_delta2) || (opts->stride == 3 && !dfa->d_delta3)))
         return AC_ERR_INVALID_ARG;

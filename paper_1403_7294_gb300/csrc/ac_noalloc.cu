@@ -60,6 +60,7 @@ extern "C" int ac_scan_noalloc(const ac_dfa* dfa, const ac_text* text, ac_result
     if (text->n_bases && (!text->data || (reinterpret_cast<uintptr_t>(text->data) & 15))) return AC_ERR_INVALID_ARG;
     if (text->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
     if (r->capacity && !r->matches) return AC_ERR_INVALID_ARG;
+    if (r->on_device && (reinterpret_cast<uintptr_t>(r->matches) & 15)) return AC_ERR_INVALID_ARG;  // 16-byte records
     // the launch-shape options ac_scan accepts, and the table a requested stride reads
     if (!ac_valid_shape_opts(opts) || !ac_stride_tables_present(dfa, opts)) return AC_ERR_INVALID_ARG;
     const HostTables& h = dfa->host;

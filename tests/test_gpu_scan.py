@@ -287,3 +287,24 @@ def test_autotune_picks_a_chunk_and_stays_exact():
     r = acg.scan(d, packed, encoding=N.AC_TEXT_PACKED2, n_bases=len(text), stats=True)  # the tuned shape
     assert_same(r, want, counts)
     assert (r.stats["chunks_per_lane"], r.stats["chunk"]) == (best["chunks_per_lane"], best["chunk"])
+
+
+def test_misaligned_device_results_are_refused():
+    """Occurrences are written as whole 16-byte records, so a device result buffer that is not
+    16-byte aligned is refused before anything runs (no write is attempted)."""
+    import ctypes
+
+    d = acg.build([b"ACGT"])
+    text = acg.pack(to_dev(b"ACGT" * 100))
+    raw = torch.zeros(256, dtype=torch.int64, device=DEV)
+    desc = N.Text(text.data_ptr(), 400, N.AC_TEXT_PACKED2, 1)
+    for off in (8, 4):
+        r = N.Result(raw.data_ptr() + off, 64, 0, None, 1, 0, 0)
+        L = acg.lib()
+        assert L.ac_scan(d.h, ctypes.byref(desc), ctypes.byref(r), None, None, None) == N.AC_ERR_INVALID_ARG
+        assert L.ac_scan_noalloc(d.h, ctypes.byref(desc), ctypes.byref(r), None, None) == N.AC_ERR_INVALID_ARG
+        descs = (N.Text * 1)(desc)
+        assert L.ac_scan_batch(d.h, descs, 1, ctypes.byref(r), None, None, None) == N.AC_ERR_INVALID_ARG
+    r = N.Result(raw.data_ptr(), 128, 0, None, 1, 0, 0)  # aligned: fine
+    assert acg.lib().ac_scan(d.h, ctypes.byref(desc), ctypes.byref(r), None, None, None) == N.AC_OK
+    assert r.n_matches == 100
