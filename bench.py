@@ -329,8 +329,8 @@ def run_plain(args, world, rank, local):
                    "step time = device time of each ac_scan call") if flush is not None
                   else f"inputs larger than L2 ({n // 4 / 1e6:.0f} MB packed text vs 129 MB L2)",
             "parallelism": f"replicas x{world}", "build_ms": round(dfa.info["build_ms"], 1),
-            "shape": {k: getattr(stats, k) for k in ("stride", "chunk", "threads", "interleave", "hot_states", "grid",
-                                                     "blocks_per_sm")},
+            "shape": {k: getattr(stats, k) for k in ("stride", "chunk", "chunks_per_lane", "threads", "interleave",
+                                                     "hot_states", "grid", "blocks_per_sm")},
             "autotuned": not args.shape,
         },
         "gpu_launches": (3 if ascii_input else 2) * args.steps,  # (pack kernel +) scan kernel + count kernel per step
