@@ -519,7 +519,7 @@ void ac_serve_destroy(ac_server* srv);
  *
  * ac_fault_inject sets the process-wide fault plan, replacing any earlier
  * plan (and the AC_FAULT environment variable, which is read once, at the
- * library's first allocation, when no plan was set). spec is a
+ * library's first allocation or kernel launch, when no plan was set). spec is a
  * comma-separated list of
  *   "oom@k"       the k-th device allocation (k >= 1) of the library from now
  *                 on fails as if the device were full: the call that made it

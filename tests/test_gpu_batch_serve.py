@@ -420,7 +420,7 @@ def test_serve_split_batch_results_taken_without_copy():
     d = acg.build(pats)
     srv = acg.Server(n_streams=1, max_batch=32)
     slot = srv.add_dfa(d)
-    big = np.frombuffer(rand_dna(rng, 1 << 20) * 64, np.uint8)  # keeps the one worker busy meanwhile
+    big = np.frombuffer(rand_dna(rng, 1 << 20) * 192, np.uint8)  # keeps the one worker busy meanwhile
     d_big = acg.build([b"ACGTACGTAC"])
     s_big = srv.add_dfa(d_big)
     t_big = srv.submit(s_big, big)
