@@ -401,3 +401,41 @@ def test_fault_plan_parsing_on_the_host():
     for bad in (b"oom", b"oom@0", b"oom@-2", b"oom@x", b"leak@1", b"oom@1;cuda_err@2", b"oom@1,"):
         assert lib.ac_fault_inject(bad) == N.AC_ERR_INVALID_ARG
     assert lib.ac_fault_inject(None) == N.AC_OK
+
+
+# C type of each ctypes mirror in _native.py
+C_STRUCTS = {"BuildOpts": "ac_build_opts", "DfaInfo": "ac_dfa_info_t", "DfaTables": "ac_dfa_tables_t", "Text": "ac_text",
+             "Match": "ac_match", "Result": "ac_result", "ScanOpts": "ac_scan_opts", "ScanStats": "ac_scan_stats",
+             "ServeOpts": "ac_serve_opts", "Served": "ac_served", "ServeStats": "ac_serve_stats_t",
+             "MemUsage": "ac_mem_usage_t"}
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C compiler gives the
+    header's struct (compiled here with gcc)."""
+    import ctypes
+    import shutil
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for py, c in C_STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in getattr(N, py)._fields_:
+            lines.append(f'printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            py, name, v = line.split()
+            got[(py, name)] = int(v)
+    for py in C_STRUCTS:
+        cls = getattr(N, py)
+        assert got[(py, "size")] == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert got[(py, name)] == getattr(cls, name).offset, (py, name)

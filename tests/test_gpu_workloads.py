@@ -13,7 +13,9 @@ picks it).
     out under launch shapes reading one, two and three bases per lookup;
   * 4,096 lognormal texts, 50,000 keywords: the graph-replayed batch and the
     per-text loop against the oracle on every text;
-  * the 8 serving sets: every request alone and in the mix against the oracle.
+  * the 8 serving sets: every request alone and in the mix against the oracle,
+    on a small genome, and 256 requests of the benchmark's own stream over its
+    64 Mbase serving genome.
 """
 import os
 
@@ -169,4 +171,42 @@ def test_serving_sets_alone_vs_mix():
         want, counts = wants[i]
         assert np.array_equal(b, want) and np.array_equal(mix[i][1], counts), f"request {i} in the mix"
         assert np.array_equal(a, want) and np.array_equal(alone[1], counts), f"request {i} alone"
+    srv.close()
+
+
+def test_serving_at_benchmark_sizes_against_the_oracle():
+    """The serving workload as the benchmark builds it: the 64 Mbase serving genome, the 8
+    resident machines (1,000 to 100,000 keywords) and requests from the benchmark's own stream
+    (1 kbase to 10 Mbase, the same seed), submitted at once so that batches of several requests
+    form beside single ones; every request's occurrences and counts against the oracle."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    genome = synth.markov_text(64 << 20, synth.BASE_SEED + 4, device="cuda")
+    sets = synth.serve_sets(genome.ascii)
+    g = genome.ascii.cpu().numpy()
+    del genome
+    dfas = [acg.build(s) for s in sets]
+    n_req = 256
+    _, lens, offs, which = synth.serve_requests(n_req, synth.BASE_SEED + 5, len(g))
+    srv = acg.Server(device_budget_bytes=40 << 30, n_streams=4, max_batch=256)
+    slots = [srv.add_dfa(d) for d in dfas]
+    tickets = [srv.submit(slots[int(s)], g[int(o) : int(o) + int(n)]) for s, o, n in zip(which, offs, lens)]
+    got = [srv.wait(t, slots[int(s)]) for t, s in zip(tickets, which)]
+    st = srv.stats()
+    assert st["completed"] == n_req and st["failed"] == 0
+    assert st["batches_launched"] < n_req  # some requests were batched together
+    machines = {s: oracle.Machine(sets[s]) for s in set(int(x) for x in which)}  # shared (read only)
+
+    def want_of(i):
+        s, o, n = int(which[i]), int(offs[i]), int(lens[i])
+        pos, pid, c = machines[s].scan(g[o : o + n])
+        a = np.stack([pos.astype(np.int64), pid.astype(np.int64)], 1)
+        return a[np.lexsort((a[:, 1], a[:, 0]))], c.astype(np.int64)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        for i, (want, counts) in enumerate(ex.map(want_of, range(n_req))):
+            m, c, k = got[i]
+            assert k == len(want), f"request {i}"
+            assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want), f"request {i}"
+            assert np.array_equal(c, counts), f"request {i}"
     srv.close()
