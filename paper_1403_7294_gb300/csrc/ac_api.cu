@@ -1600,14 +1600,23 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
     cudaStream_t cap = nullptr;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     int rc = AC_OK;
+    // with counts, the count kernel sets the per-state hit counters back to 0
+    // as it reads them, so replays start from zeroed counters without a memset
+    if (d_counts && ((e = cudaMemsetAsync(p->d_hits, 0, (size_t)h.n_states * 8, cap)) != cudaSuccess ||
+                     (e = cudaStreamSynchronize(cap)) != cudaSuccess)) {
+        cudaStreamDestroy(cap);
+        return fail(e);
+    }
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(p->d_ctr, 0, 4 * 8, cap);
-        cudaMemsetAsync(p->d_hits, 0, (size_t)h.n_states * 8, cap);
+        if (!d_counts) cudaMemsetAsync(p->d_hits, 0, (size_t)h.n_states * 8, cap);
         rc = ac_launch_batch(a, sh, cap);
         if (d_counts) {
             cudaMemsetAsync(d_counts, 0, (size_t)h.n_patterns * 8, cap);
-            if (!rc) rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states, p->d_hits, d_counts, cap);
+            if (!rc)
+                rc = ac_launch_counts(dfa->d_out_off, reinterpret_cast<const uint2*>(dfa->d_out_ent), h.n_states,
+                                      p->d_hits, d_counts, cap, true);
         }
         cudaMemcpyAsync(p->h_pad, p->d_ctr, 8, cudaMemcpyDeviceToHost, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &p->graph);

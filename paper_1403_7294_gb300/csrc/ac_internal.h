@@ -123,8 +123,10 @@ struct ScanArgs {
 int ac_launch_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, bool fold,
                    unsigned long long* bad, void* stream);
 int ac_launch_scan(const ScanArgs& a, const ScanShape& sh, void* stream);
+// clear_hits: set every counter read back to 0 (hits must then be writable).
 int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_states,
-                     const unsigned long long* hits, unsigned long long* counts, void* stream);
+                     const unsigned long long* hits, unsigned long long* counts, void* stream,
+                     bool clear_hits = false);
 // Copies n packed bases from base src_off of src to base dst_off of dst.
 int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint64_t src_off, uint64_t n,
                      void* stream);

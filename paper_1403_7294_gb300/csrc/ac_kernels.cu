@@ -955,14 +955,15 @@ __global__ void splice_kernel(uint32_t* __restrict__ dst, uint64_t dst_off, cons
     }
 }
 
-// counts[p] = sum over states s with p in output(s) of hits[s]
+// counts[p] = sum over states s with p in output(s) of hits[s]; with clear,
+// each counter read is set back to 0 (for buffers that the next scan reuses).
 __global__ void counts_kernel(const uint32_t* __restrict__ out_off, const uint2* __restrict__ out_ent,
-                              uint32_t n_states, const unsigned long long* __restrict__ hits,
-                              unsigned long long* counts) {
+                              uint32_t n_states, unsigned long long* hits, unsigned long long* counts, int clear) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_states; s += stride) {
         const unsigned long long h = hits[s];
         if (!h) continue;
+        if (clear) hits[s] = 0ull;
         for (uint32_t k = out_off[s]; k < out_off[s + 1]; ++k) atomicAdd(&counts[out_ent[k].x], h);
     }
 }
@@ -1330,14 +1331,16 @@ int ac_launch_splice(uint32_t* dst, uint64_t dst_off, const uint32_t* src, uint6
 }
 
 int ac_launch_counts(const uint32_t* out_off, const uint2* out_ent, uint32_t n_states,
-                     const unsigned long long* hits, unsigned long long* counts, void* stream) {
+                     const unsigned long long* hits, unsigned long long* counts, void* stream, bool clear_hits) {
     if (n_states == 0) return 0;
     const DeviceProps& p = ac_device_props();
     uint32_t blocks = (n_states + 255) / 256;
     const uint32_t cap = (uint32_t)p.sms * 8;
     if (blocks > cap) blocks = cap;
     if (ac_fault_launch()) return (int)cudaErrorLaunchFailure;
-    counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_ent, n_states, hits, counts);
+    counts_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(out_off, out_ent, n_states,
+                                                            const_cast<unsigned long long*>(hits), counts,
+                                                            clear_hits ? 1 : 0);
     return (int)cudaGetLastError();
 }
 

@@ -108,12 +108,25 @@ def test_batch_plan_replays_exactly(chunk, stride, threads):
     plan.close()
 
 
+def test_batch_plan_without_counts_replays_exactly():
+    texts, pats = batch_case(17, 60)
+    d = acg.build(pats)
+    want, _ = oracle_batch(pats, texts)
+    plan = acg.BatchPlan(d, packed_dev(texts), [len(t) for t in texts], capacity=len(want) + 10, counts=False)
+    for _ in range(3):
+        assert plan.run() == len(want)
+        assert np.array_equal(plan.result().canonical(), want)
+    plan.close()
+
+
 def test_batch_plan_overflow_flag():
     texts = [b"A" * 1000, b"A" * 10]
     d = acg.build([b"A", b"AA"])
     plan = acg.BatchPlan(d, packed_dev(texts), [1000, 10], capacity=100)
-    assert plan.run() == 1000 + 999 + 10 + 9 and plan.overflow
-    assert plan.counts.cpu().tolist() == [1010, 1008]
+    for _ in range(3):  # counts stay exact when replays overflow
+        assert plan.run() == 1000 + 999 + 10 + 9 and plan.overflow
+        assert plan.counts.cpu().tolist() == [1010, 1008]
+    plan.close()
 
 
 # ------------------------------------------------------------------ serving
