@@ -68,9 +68,21 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     return p;
 }
 
+// A table entry, read from L2 under the given policy. With InL1 false the
+// entry is not allocated in L1: a long chunk's walk spreads its rows over
+// megabytes, so one SM almost never reads a row twice while it is in L1, and
+// allocating them would push out the text lines and output entries that are
+// read again (plain scans, measured: about 2% faster on the 3 Gbase genome and
+// the 256 Mbase chromosome). The batch kernel keeps allocating them: its lanes
+// restart from the root every few hundred bases, and without L1 its kernel on
+// 4,096 short texts took about 5% longer.
+template <bool InL1>
 __device__ __forceinline__ uint32_t ld_table(const uint32_t* p, uint64_t pol) {
     uint32_t v;
-    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    if constexpr (InL1)
+        asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
 
@@ -347,7 +359,7 @@ constexpr int wide_build(uint32_t threads) {
 
 // Walk I chains in lockstep, ST bases per lookup (all 32 lanes of the warp
 // call this together). q: this warp's event queue in shared memory.
-template <int I, int ST>
+template <int I, int ST, bool InL1>
 __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                      const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab, uint64_t pol_txt) {
     constexpr uint32_t ROW_SHIFT = ST == 1 ? 2 : 4;  // log2 entries per row
@@ -395,10 +407,10 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
                     const uint32_t sym = (wd[j] >> (2 * ST * k)) & SYM_MASK;
                     const uint32_t idx = (s[j] << ROW_SHIFT) | sym;
                     if (ST == 1 || s[j] < tb.s2_rows) {
-                        e[j] = (s[j] < hot) ? sm[idx] : ld_table(table + idx, pol_tab);
+                        e[j] = (s[j] < hot) ? sm[idx] : ld_table<InL1>(table + idx, pol_tab);
                     } else {  // deep state without a two-base row: two one-base lookups
-                        const uint32_t e1 = ld_table(tb.delta + ((s[j] << 2) | (sym & 3u)), pol_tab);
-                        const uint32_t e2 = ld_table(tb.delta + (((e1 & AC_STATE_MASK) << 2) | (sym >> 2)), pol_tab);
+                        const uint32_t e1 = ld_table<InL1>(tb.delta + ((s[j] << 2) | (sym & 3u)), pol_tab);
+                        const uint32_t e2 = ld_table<InL1>(tb.delta + (((e1 & AC_STATE_MASK) << 2) | (sym >> 2)), pol_tab);
                         e[j] = e2 | ((e1 & AC_FLAG) >> 1);  // bit 31: final state, bit 30: after the first base
                     }
                 }
@@ -442,7 +454,7 @@ __device__ __forceinline__ void walk(const Chain (&ch)[I], const uint32_t* __res
 // 30, 31 after the first, second, third base; two-base rows: bits 30, 31).
 // Each lane reads its text through a 64-base block, the next block already
 // loading, into a bit buffer of the coming bases.
-template <int I>
+template <int I, bool InL1>
 __device__ __forceinline__ void walk3_free(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                            const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
                                            uint64_t pol_txt) {
@@ -505,7 +517,7 @@ __device__ __forceinline__ void walk3_free(const Chain (&ch)[I], const uint32_t*
                 idx = (cs << 2) | (sym[j] & 3u);
                 tab = tb.delta;
             }
-            e[j] = act[j] ? ((cs < hot) ? sm[idx] : ld_table(tab + idx, pol_tab)) : 0u;
+            e[j] = act[j] ? ((cs < hot) ? sm[idx] : ld_table<InL1>(tab + idx, pol_tab)) : 0u;
         }
         uint32_t any = 0, nx[I];
         bool fin[I], m1[I], m2[I];
@@ -555,7 +567,7 @@ __device__ __forceinline__ void walk3_free(const Chain (&ch)[I], const uint32_t*
 // through L1: a lane's next groups come from the same cached line. The step
 // loop is not unrolled (its three append sites per step made the unrolled
 // body large enough to slow the emission-heavy regions).
-template <int I>
+template <int I, bool InL1>
 __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                            const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
                                            uint64_t pol_txt) {
@@ -591,7 +603,7 @@ __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t*
             for (int j = 0; j < I; ++j) {
                 sy[j] = w[j][0] & 63u;  // the next three bases
                 const uint32_t idx = (s[j] << 6) | sy[j];
-                e[j] = (s[j] < hot) ? sm[idx] : ld_table(tb.delta3 + idx, pol_tab);
+                e[j] = (s[j] < hot) ? sm[idx] : ld_table<InL1>(tb.delta3 + idx, pol_tab);
             }
             uint32_t any = 0;
 #pragma unroll
@@ -632,16 +644,16 @@ __device__ __forceinline__ void walk3_lock(const Chain (&ch)[I], const uint32_t*
 // lookup; 3 the three-base walk with lanes on their own schedules; 4 the
 // lockstep three-base walk, used when every state has a three-base row (the
 // launchers pick 3 or 4 for a requested stride of 3).
-template <int I, int ST>
+template <int I, int ST, bool InL1>
 __device__ __forceinline__ void walk_any(const Chain (&ch)[I], const uint32_t* __restrict__ sm, uint32_t hot,
                                          const Tables& tb, const Emit* em, uint4* q, uint64_t pol_tab,
                                          uint64_t pol_txt) {
     if constexpr (ST == 4)
-        walk3_lock<I>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+        walk3_lock<I, InL1>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
     else if constexpr (ST == 3)
-        walk3_free<I>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+        walk3_free<I, InL1>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
     else
-        walk<I, ST>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
+        walk<I, ST, InL1>(ch, sm, hot, tb, em, q, pol_tab, pol_txt);
 }
 
 // Copies `rows16` 16-byte rows (the hot prefix of the table) to shared memory.
@@ -680,7 +692,7 @@ __global__ void __launch_bounds__(Bounds<I, ST, W>::threads, Bounds<I, ST, W>::b
                 idle_chain(ch[j], a.text, nwords, a.text_id);
             }
         }
-        walk_any<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        walk_any<I, ST, false>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -722,7 +734,7 @@ __global__ void __launch_bounds__(Bounds<I, ST, W>::threads, Bounds<I, ST, W>::b
                 set_chain(ch[j], bt.words, (bt.n + 15) >> 4, lo_t, lo, min(lo + a.chunk, bt.n), a.halo);
             }
         }
-        walk_any<I, ST>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
+        walk_any<I, ST, true>(ch, sm, hot, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -760,7 +772,7 @@ __global__ void __launch_bounds__(MaxThreads<I>::value) part_scan_kernel(PartArg
                 idle_chain(ch[j], a.text, nwords, 0u);
             }
         }
-        walk<I, 1>(ch, sm, pd.n_states, tb, &em, q, pol_tab, pol_txt);
+        walk<I, 1, true>(ch, sm, pd.n_states, tb, &em, q, pol_tab, pol_txt);
     }
 }
 
@@ -797,7 +809,7 @@ __global__ void __launch_bounds__(1024) failureless_kernel(FlArgs a, uint32_t ho
             if (alive && p < a.n) {
                 const uint32_t c = (__ldg(a.text + (p >> 4)) >> (2 * (p & 15))) & 3u;
                 const uint32_t idx = (s << 2) | c;
-                e = (s < hot) ? sm[idx] : ld_table(a.gotos + idx, pol_tab);
+                e = (s < hot) ? sm[idx] : ld_table<true>(a.gotos + idx, pol_tab);
             }
             alive = alive && (e & AC_STATE_MASK31) != AC_NO_EDGE;
             if (alive) s = e & AC_STATE_MASK31;
