@@ -947,18 +947,31 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint3
 }
 
 // Copies n bases of a packed text from base src_off of src to base dst_off
-// of dst (any offsets). One thread per destination word: it rewrites only
-// the bases of the range and keeps the other bases of its word.
+// of dst (any offsets). One thread per destination word. A word wholly inside
+// the range is the 16 source bases starting at its first base: one funnel
+// shift of the (at most two) source words that hold them. The (at most two)
+// edge words rewrite only the bases of the range, base by base, and keep the
+// other bases of the word.
 __global__ void splice_kernel(uint32_t* __restrict__ dst, uint64_t dst_off, const uint32_t* __restrict__ src,
                               uint64_t src_off, uint64_t n) {
     const uint64_t w0 = dst_off >> 4, w1 = (dst_off + n + 15) >> 4;
+    const uint64_t end = dst_off + n;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t w = w0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+        const uint64_t p0 = w << 4;
+        if (p0 >= dst_off && p0 + 16 <= end) {
+            const uint64_t q0 = src_off + (p0 - dst_off);  // source of this word's first base
+            const uint32_t sh = 2u * (uint32_t)(q0 & 15);
+            const uint32_t lo = __ldg(src + (q0 >> 4));
+            // with sh > 0 the word's last base, q0 + 15 < src_off + n, lies in the next source word
+            dst[w] = sh ? __funnelshift_r(lo, __ldg(src + (q0 >> 4) + 1), sh) : lo;
+            continue;
+        }
         uint32_t word = dst[w];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const uint64_t p = (w << 4) + j;
-            if (p < dst_off || p >= dst_off + n) continue;
+            const uint64_t p = p0 + j;
+            if (p < dst_off || p >= end) continue;
             const uint64_t q = src_off + (p - dst_off);
             const uint32_t b = (__ldg(src + (q >> 4)) >> (2 * (q & 15))) & 3u;
             word = (word & ~(3u << (2 * j))) | (b << (2 * j));

@@ -79,3 +79,27 @@ def test_stream_reset_and_alphabet_error_keep_state():
     again = s.scan(text).canonical()
     assert np.array_equal(again, want)
     s.close()
+
+
+@pytest.mark.parametrize("lmax", list(range(2, 35)))
+def test_stream_every_carry_offset(lmax):
+    """The carried L_max-1 bases put the next piece at every offset within a
+    packed word (the splice's word-shift path and its edge words)."""
+    rng = random.Random(700 + lmax)
+    text = bytes(rng.choice(b"ACGT") for _ in range(3_000)) + b"ACGTACGTAC" * 20
+    pats = [text[j : j + rng.randint(1, lmax)] for j in rng.sample(range(len(text) - 40), 60)]
+    pats.append(text[100 : 100 + lmax])
+    d = acg.build(pats)
+    want, counts = oracle_canonical(pats, text)
+    s = acg.Stream(d)
+    rows, csum = [], np.zeros(len(pats), np.int64)
+    for a, b in _pieces(rng, len(text), lmax):
+        packed = acg.pack(torch.tensor(list(text[a:b]), dtype=torch.uint8, device="cuda"))
+        r = s.scan(packed, encoding=N.AC_TEXT_PACKED2, n_bases=b - a)
+        rows.append(r.canonical())
+        csum += r.counts.cpu().numpy()
+    got = np.concatenate(rows)
+    got = got[np.lexsort((got[:, 2], got[:, 1], got[:, 0]))]
+    assert np.array_equal(got, want)
+    assert csum.tolist() == counts.tolist()
+    s.close()
