@@ -756,6 +756,9 @@ extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, con
 namespace {
 
 constexpr int kPipeMaxPieces = 64;
+// The first piece is short, so that its occurrences, and with them the copy-out
+// that bounds the whole call, start after a short copy-in and scan.
+constexpr uint64_t kPipeFirstPiece = 8ull << 20;
 
 struct CopyStreams {
     cudaStream_t in = nullptr, out = nullptr;
@@ -826,7 +829,8 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
     int k = 0;
     for (uint64_t a = own_begin, b = 0; a < own_end && status == AC_OK; a = b, ++k) {
         // piece boundaries on absolute 64-base multiples (word-aligned packing); the last takes the rest
-        b = (k == kPipeMaxPieces - 1) ? own_end : std::min<uint64_t>(own_end, (a + piece) & ~63ull);
+        const uint64_t step = k == 0 ? std::min<uint64_t>(piece, kPipeFirstPiece) : piece;
+        b = (k == kPipeMaxPieces - 1) ? own_end : std::min<uint64_t>(own_end, (a + step) & ~63ull);
         const uint64_t upto = (b == own_end) ? n : b;  // bases the piece needs
         // ---- copy in [copied, upto)
         if (upto > copied) {

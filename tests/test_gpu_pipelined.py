@@ -27,7 +27,9 @@ from paper_1403_7294_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 PIECE = 256 << 20  # owned bases per piece of the overlapped host path
-N_BASES = (640 << 20) + 12_345  # two full pieces and a ragged third
+FIRST = 8 << 20  # its first piece is short
+N_BASES = (640 << 20) + 12_345  # a short piece, two full pieces and a ragged fourth
+BOUNDS = [FIRST, FIRST + PIECE, FIRST + 2 * PIECE]  # where pieces meet
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +101,7 @@ def test_piece_boundaries_against_oracle(work):
     end = pos + lens[pid] - 1
     m = oracle.Machine(pats)
     win = 1 << 20
-    starts = [PIECE - win, 2 * PIECE - win, N_BASES - win, 0]
+    starts = [b - win // 2 for b in BOUNDS] + [b - win for b in BOUNDS] + [N_BASES - win, 0]
     starts += random.Random(7).sample(range(0, N_BASES - win), 3)
     for s0 in starts:
         s1 = s0 + win
@@ -115,7 +117,7 @@ def test_piece_boundaries_against_oracle(work):
         assert np.array_equal(g, w), f"window at {s0}"
 
 
-@pytest.mark.parametrize("where", [[300_000_000, N_BASES - 5], [N_BASES - 5], [PIECE]])
+@pytest.mark.parametrize("where", [[300_000_000, N_BASES - 5], [N_BASES - 5], [FIRST], [FIRST + PIECE], [5]])
 def test_bad_byte_absolute_offset(work, where):
     pats, d, dev, host, want = work
     old = [int(host[i]) for i in where]
