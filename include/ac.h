@@ -476,7 +476,8 @@ int ac_serve_add_dfa(ac_server* srv, const ac_dfa* dfa, uint32_t* slot);
 /* Queues a scan of a HOST text (ASCII or packed) against dfa `slot`; the
  * bases are copied during the call, so the caller may reuse its buffer.
  * Returns AC_ERR_BUSY when the queue is full or the text alone exceeds the
- * device budget. */
+ * device budget, AC_ERR_ALPHABET when an ASCII text holds a byte other than
+ * A, C, G, T (checked while it is copied; nothing is queued). */
 int ac_serve_submit(ac_server* srv, uint32_t slot, const ac_text* text, uint64_t* ticket);
 /* Waits up to timeout_us (<0: forever) for a ticket. On completion copies
  * the occurrences (with text_id 0) and the counts into the HOST buffers of

@@ -143,29 +143,120 @@ uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
 // handed to the request; smaller ones go through the worker's buffers.
 constexpr size_t kHandoffBytes = (size_t)1 << 20;
 
-// Whether every byte is one of A, C, G, T: 64 bytes per step through the
-// compiler's generic 16-byte vectors (no target-specific code; the host
+// Copies n bytes from src to dst; with `check`, also tells whether every byte
+// is one of A, C, G, T. One pass over the caller's bytes: 64 per step through
+// the compiler's generic 16-byte vectors (no target-specific code; the host
 // compiler maps them to the machine's SIMD registers), the tail byte by byte.
 typedef uint8_t v16u8 __attribute__((vector_size(16)));
 typedef int8_t v16i8 __attribute__((vector_size(16)));
 
-bool all_acgt(const uint8_t* b, uint64_t n) {
+bool copy_text(uint8_t* dst, const uint8_t* src, uint64_t n, bool check) {
+    if (!check) {
+        if (n) std::memcpy(dst, src, n);
+        return true;
+    }
     uint64_t i = 0;
+    v16i8 bad = {};
     for (; i + 64 <= n; i += 64) {
-        v16i8 bad = {};
         for (int k = 0; k < 4; ++k) {
             v16u8 x;
-            std::memcpy(&x, b + i + 16 * k, 16);
+            std::memcpy(&x, src + i + 16 * k, 16);
             bad |= (x != 'A') & (x != 'C') & (x != 'G') & (x != 'T');  // lanes: -1 where not a base
+            std::memcpy(dst + i + 16 * k, &x, 16);
         }
-        uint64_t w[2];
-        std::memcpy(w, &bad, 16);
-        if (w[0] | w[1]) return false;
     }
-    for (; i < n; ++i)
-        if (b[i] != 'A' && b[i] != 'C' && b[i] != 'G' && b[i] != 'T') return false;
-    return true;
+    uint64_t w[2];
+    std::memcpy(w, &bad, 16);
+    bool ok = (w[0] | w[1]) == 0;
+    for (; i < n; ++i) {
+        const uint8_t c = src[i];
+        dst[i] = c;
+        ok &= c == 'A' || c == 'C' || c == 'G' || c == 'T';
+    }
+    return ok;
 }
+
+// Large submitted texts are copied (and checked) by the submitting thread
+// together with a few helper threads of the server, each taking one
+// contiguous part: one core's memory copy would otherwise be most of the
+// time a large request spends in ac_serve_submit.
+constexpr uint64_t kSplitCopyBytes = 2ull << 20;  // smaller texts: the caller's thread alone
+constexpr int kCopyHelpers = 3;
+
+class CopyHelpers {
+   public:
+    CopyHelpers() {
+        try {
+            for (int i = 0; i < kCopyHelpers; ++i) threads_.emplace_back([this] { run(); });
+        } catch (...) {  // fewer helpers (none at worst): copy() splits over the ones running
+        }
+    }
+    ~CopyHelpers() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : threads_) t.join();
+    }
+    // copy_text over (helpers + 1) parts; true when every part passed the check
+    bool copy(uint8_t* dst, const uint8_t* src, uint64_t n, bool check) {
+        const uint64_t parts = threads_.size() + 1;
+        if (parts == 1 || n < kSplitCopyBytes) return copy_text(dst, src, n, check);
+        const uint64_t part = round_up((n + parts - 1) / parts, 64);
+        Job job;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            for (uint64_t i = 0; i + 1 < parts; ++i) {
+                const uint64_t a = std::min(n, i * part), b = std::min(n, a + part);
+                tasks_.push_back(Task{&job, dst + a, src + a, b - a, check});
+                ++job.pending;
+            }
+        }
+        cv_.notify_all();
+        const uint64_t a = std::min(n, (parts - 1) * part);
+        const bool ok = copy_text(dst + a, src + a, n - a, check);
+        std::unique_lock<std::mutex> lk(job.mu);
+        job.cv.wait(lk, [&] { return job.pending == 0; });
+        return ok && job.ok;
+    }
+
+   private:
+    struct Job {
+        std::mutex mu;
+        std::condition_variable cv;
+        int pending = 0;
+        bool ok = true;
+    };
+    struct Task {
+        Job* job;
+        uint8_t* dst;
+        const uint8_t* src;
+        uint64_t n;
+        bool check;
+    };
+    void run() {
+        for (;;) {
+            Task t;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || !tasks_.empty(); });
+                if (tasks_.empty()) return;  // stopping, nothing left to copy
+                t = tasks_.front();
+                tasks_.pop_front();
+            }
+            const bool ok = copy_text(t.dst, t.src, t.n, t.check);
+            std::lock_guard<std::mutex> lk(t.job->mu);  // the waiter wakes only after this is released
+            t.job->ok = t.job->ok && ok;
+            if (--t.job->pending == 0) t.job->cv.notify_one();
+        }
+    }
+    std::vector<std::thread> threads_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<Task> tasks_;
+    bool stop_ = false;
+};
 
 struct PinnedBuf {
     void* p = nullptr;
@@ -205,6 +296,7 @@ struct ac_server {
     uint32_t in_flight_reqs = 0;
     bool stop = false;
     std::vector<std::thread> workers;
+    CopyHelpers copiers;  // threads that share the copy of large submitted texts
     // stats
     uint64_t submitted = 0, completed = 0, rejected = 0, failed = 0, bases_completed = 0, batches = 0;
     uint64_t overflow_batches = 0;  // batches run twice for want of output room
@@ -560,8 +652,6 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
     if (t->encoding != AC_TEXT_ASCII && t->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
     if (t->n_bases && !t->data) return AC_ERR_INVALID_ARG;
     if (t->n_bases >= AC_MAX_BASES) return AC_ERR_TOO_LARGE;
-    // reject bad input before it is queued
-    if (t->encoding == AC_TEXT_ASCII && !all_acgt((const uint8_t*)t->data, t->n_bases)) return AC_ERR_ALPHABET;
     auto r = std::make_shared<Request>();
     r->slot = slot;
     r->encoding = t->encoding;
@@ -579,18 +669,24 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
             return AC_ERR_BUSY;
         }
     }
+    // the text is copied now, and an ASCII text checked in the same pass: bad
+    // input is refused here, before it is queued
+    const bool ascii = t->encoding == AC_TEXT_ASCII;
+    bool ok = true;
     try {
-        const uint64_t held = t->encoding == AC_TEXT_ASCII ? round_up(t->n_bases, 64) : nb;
+        const uint64_t held = ascii ? round_up(t->n_bases, 64) : nb;
         if (nb >= kHandoffBytes) r->text_block = s->pool->get(held);  // no pinned memory: staged instead
         if (r->text_block) {
-            std::memcpy(r->text_block->p, t->data, nb);
+            ok = s->copiers.copy((uint8_t*)r->text_block->p, (const uint8_t*)t->data, nb, ascii);
             std::memset((uint8_t*)r->text_block->p + nb, 'A', held - nb);
         } else {
-            r->bytes.assign((const uint8_t*)t->data, (const uint8_t*)t->data + nb);
+            r->bytes.resize(nb);
+            ok = copy_text(r->bytes.data(), (const uint8_t*)t->data, nb, ascii);
         }
     } catch (const std::bad_alloc&) {
         return AC_ERR_OOM;
     }
+    if (!ok) return AC_ERR_ALPHABET;  // the request and its block go with r
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

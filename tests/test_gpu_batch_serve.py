@@ -323,6 +323,26 @@ def test_serve_submit_alphabet_check():
                 with pytest.raises(acg.AcError) as e:
                     srv.submit(slot, bytes(t))
                 assert e.value.status == N.AC_ERR_ALPHABET, (n, pos, v)
+    big = bytearray(rand_dna(rng, (1 << 20) + 77))  # held in a pinned block from submit on
+    for pos in (0, 63, 64, 4097, len(big) // 2, len(big) - 78, len(big) - 1):
+        t = bytearray(big)
+        t[pos] = ord("N")
+        with pytest.raises(acg.AcError) as e:
+            srv.submit(slot, bytes(t))
+        assert e.value.status == N.AC_ERR_ALPHABET, pos
+    # texts of 2 MB and more are copied in four parts of round_up(n / 4, 64) bytes: a bad byte at
+    # either side of every part boundary, and a good text exact against the oracle
+    huge = bytearray(rand_dna(rng, (4 << 20) + 333))
+    part = ((len(huge) + 3) // 4 + 63) // 64 * 64
+    for pos in (0, part - 1, part, 2 * part - 1, 2 * part, 3 * part - 1, 3 * part, len(huge) - 1):
+        t = bytearray(huge)
+        t[pos] = ord("a")
+        with pytest.raises(acg.AcError) as e:
+            srv.submit(slot, bytes(t))
+        assert e.value.status == N.AC_ERR_ALPHABET, pos
+    m, c, k = srv.wait(srv.submit(slot, bytes(huge)), slot)
+    want, counts = oracle_canonical([b"ACGT"], bytes(huge))
+    assert np.array_equal(m[np.lexsort((m[:, 1], m[:, 0]))], want[:, 1:]) and c.tolist() == counts.tolist()
     good = rand_dna(rng, 100_003)
     m, c, k = srv.wait(srv.submit(slot, good), slot)
     want, counts = oracle_canonical([b"ACGT"], good)
