@@ -205,12 +205,12 @@ class CopyHelpers {
         if (parts == 1 || n < kSplitCopyBytes) return copy_text(dst, src, n, check);
         const uint64_t part = round_up((n + parts - 1) / parts, 64);
         Job job;
+        job.pending = (int)(parts - 1);  // set before any helper can see a task of this job
         {
             std::lock_guard<std::mutex> lk(mu_);
             for (uint64_t i = 0; i + 1 < parts; ++i) {
                 const uint64_t a = std::min(n, i * part), b = std::min(n, a + part);
                 tasks_.push_back(Task{&job, dst + a, src + a, b - a, check});
-                ++job.pending;
             }
         }
         cv_.notify_all();
