@@ -454,7 +454,7 @@ ScanShape ac_default_shape(const ac_dfa* dfa, uint64_t owned, const ac_scan_opts
     sh.hot = std::min(std::min(sh.hot, h.n_states), max_hot);
     if (sh.stride == 2) sh.hot = std::min(sh.hot, h.s2_rows);  // staged from the two-base rows
     if (sh.stride == 3) sh.hot = std::min(sh.hot, h.s3_rows);  // staged from the three-base rows
-    sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh));
+    sh.blocks_per_sm = std::max(1u, ac_blocks_per_sm(sh, h.s3_rows >= h.n_states));
     const uint64_t lanes = (uint64_t)p.sms * sh.blocks_per_sm * sh.threads * sh.interleave;
     if (!sh.chunk) {
         if (!sh.cpl) sh.cpl = 1;  // one chunk per lane unless tuned or asked otherwise

@@ -145,8 +145,9 @@ uint32_t ac_wide_threads(uint32_t interleave, uint32_t stride);
 uint32_t ac_max_hot_states(uint32_t threads, uint32_t stride);
 // Dynamic shared memory of a scan block: hot rows plus event queues.
 size_t ac_scan_smem_bytes(uint32_t hot, uint32_t threads, uint32_t stride);
-// Resident blocks per SM for a shape (occupancy query); 0 on error.
-uint32_t ac_blocks_per_sm(const ScanShape& sh);
+// Resident blocks per SM for a shape (occupancy query of the kernel variant
+// the launch runs: all_rows3 when every state has a three-base row); 0 on error.
+uint32_t ac_blocks_per_sm(const ScanShape& sh, bool all_rows3);
 
 // Batched scan (ac_kernels.cu)
 struct BatchText {

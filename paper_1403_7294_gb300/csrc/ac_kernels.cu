@@ -1246,21 +1246,24 @@ struct BatchLaunch {
 };
 }  // namespace
 
-uint32_t ac_blocks_per_sm(const ScanShape& sh) {
-    // occupancy depends on (device, interleave, stride, threads, shared memory): memoised
+uint32_t ac_blocks_per_sm(const ScanShape& sh, bool all_rows3) {
+    // occupancy depends on (device, interleave, kernel variant, threads, shared memory): memoised
     static std::mutex mu;
     static std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, size_t>, uint32_t> memo;
     int dev = 0;
     cudaGetDevice(&dev);
     const uint32_t stride = sh.stride ? sh.stride : 1u;
-    const auto key = std::make_tuple(dev, sh.interleave, stride, sh.threads,
+    // the kernel the launch will run: three bases per lookup runs the lockstep
+    // walk (variant 4) when every state has a three-base row
+    const uint32_t code = (stride == 3 && all_rows3) ? 4u : stride;
+    const auto key = std::make_tuple(dev, sh.interleave, code, sh.threads,
                                      ac_scan_smem_bytes(sh.hot, sh.threads, stride));
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
     }
-    const int nb = dispatch(sh.interleave, stride, Occupancy{sh});
+    const int nb = dispatch(sh.interleave, code, Occupancy{sh});
     const uint32_t r = nb > 0 ? (uint32_t)nb : 0u;
     std::lock_guard<std::mutex> lk(mu);
     memo[key] = r;

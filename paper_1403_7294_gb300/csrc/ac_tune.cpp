@@ -288,7 +288,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
                     probe.interleave = il;
                     probe.hot = hot;
                     probe.stride = sd;
-                    if (ac_blocks_per_sm(probe) == 0) continue;  // does not fit
+                    if (ac_blocks_per_sm(probe, dfa->host.s3_rows >= S) == 0) continue;  // does not fit
                     const Entry e{th, il, hot, sd, 1u, 0.f};
                     ac_scan_opts o;
                     std::memset(&o, 0, sizeof o);
