@@ -657,6 +657,14 @@ def run_batched(args, steps: int):
         bwalk = stt.bases_walked
     batch_call_ms = (time.perf_counter() - t0) * 1e3 / steps
     batch_shape = {k: getattr(stt, k) for k in ("stride", "chunk", "threads", "interleave", "hot_states", "grid")}
+    if getattr(args, "minimal", False):  # replays and batch calls only: no per-text loop, no walk-only ceiling
+        plan.close()
+        bk = float(np.mean(kern))
+        return {"workload": w.name, "texts": len(lens), "bases": total, "occurrences": n_occ,
+                "states": dfa.info["n_states"], "tuned": {**tuned, "batch_chunk": tuned_chunk}, "shape": batch_shape,
+                "graph_replay_gbases_s": round(total / (graph_ms / 1e3) / 1e9, 3),
+                "graph_replay_ms": round(graph_ms, 4), "batch_call_wall_ms": round(batch_call_ms, 4),
+                "batch_kernel_ms": round(bk, 4)}
     # the plain per-text loop: one ac_scan per text, each with its own event-timed device time
     single = [(N.Text(p.data_ptr(), n, N.AC_TEXT_PACKED2, 1)) for p, n in zip(packed, lens)]
     loop_passes = max(1, min(steps, 3))
@@ -1044,7 +1052,8 @@ def main():
     ap.add_argument("--sweep-bases", type=int, default=32_000_000,
                     help="cpu-sweep: bases of the genome text each thread count scans")
     ap.add_argument("--n-bases", type=int, default=None)
-    ap.add_argument("--minimal", action="store_true", help="scan timing only (no e2e, CPU baseline or extras)")
+    ap.add_argument("--minimal", action="store_true",
+                    help="scan timing only (no e2e, CPU baseline or extras; batch: no per-text loop or ceiling)")
     ap.add_argument("--shape", default=None,
                     help="plain workloads: fixed launch shape 'stride,threads,interleave,hot_states' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=None)
