@@ -187,11 +187,16 @@ bool ac_tuned_batch_chunk(const ac_dfa* dfa, uint64_t total, uint32_t* chunk) {
 
 namespace {
 
-// Time of one candidate: the fastest of two timed scans after one untimed.
+// Timed repetitions of a candidate after one untimed run: two, or eight when
+// the run is short (below 0.5 ms launch noise decides between close shapes).
+int timed_reps(float first_ms) { return first_ms < 0.5f ? 8 : 2; }
+
+// Time of one candidate: the fastest of its timed scans after one untimed.
 int time_scan(const ac_dfa* dfa, const ac_text* sample, const ac_scan_opts& o, ac_match* d_m, uint64_t cap,
               void* stream, float* ms, uint32_t* chunk) {
     float t_best = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    int reps = 3;
+    for (int rep = 0; rep < reps; ++rep) {
         ac_result r;
         std::memset(&r, 0, sizeof r);
         r.matches = d_m;
@@ -200,6 +205,7 @@ int time_scan(const ac_dfa* dfa, const ac_text* sample, const ac_scan_opts& o, a
         ac_scan_stats stt;
         const int s = ac_scan(dfa, sample, &r, &o, stream, &stt);
         if (s != AC_OK && s != AC_ERR_OVERFLOW) return s;
+        if (rep == 0) reps = 1 + timed_reps(stt.scan_ms);
         if (rep > 0) t_best = std::min(t_best, stt.scan_ms);
         if (chunk) *chunk = stt.chunk;
     }
@@ -376,7 +382,8 @@ extern "C" int ac_autotune_batch(const ac_dfa* dfa, const ac_text* texts, uint32
         o.chunk = c;
         float t_best = 1e30f;
         uint32_t used = c;
-        for (int rep = 0; rep < 3 && rc == AC_OK; ++rep) {
+        int reps = 3;
+        for (int rep = 0; rep < reps && rc == AC_OK; ++rep) {
             ac_result r;
             std::memset(&r, 0, sizeof r);
             r.matches = d_m;
@@ -385,6 +392,7 @@ extern "C" int ac_autotune_batch(const ac_dfa* dfa, const ac_text* texts, uint32
             ac_scan_stats stt;
             const int s = ac_scan_batch(dfa, texts, n_texts, &r, &o, stream, &stt);
             if (s != AC_OK && s != AC_ERR_OVERFLOW) rc = s;
+            if (rep == 0) reps = 1 + timed_reps(stt.scan_ms);
             if (rep > 0) t_best = std::min(t_best, stt.scan_ms);
             used = stt.chunk;
         }
