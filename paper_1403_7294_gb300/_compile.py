@@ -77,7 +77,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if lib_ok and all(os.path.getmtime(LIB) >= os.path.getmtime(os.path.join(OUT_DIR, os.path.basename(s) + ".o")) for s in srcs):
         return LIB
     objs = [os.path.join(OUT_DIR, os.path.basename(s) + ".o") for s in srcs]
-    cmd = [NVCC, "-shared", "-o", LIB] + objs + ARCH + ["-lpthread"]
+    cmd = [NVCC, "-shared", "-o", LIB] + objs + ARCH + ["-lpthread", "-ldl"]  # -ldl: NVTX loads a tool on demand
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")

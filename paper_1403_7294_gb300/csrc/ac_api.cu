@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ac_internal.h"
+#include "ac_trace.h"
 
 namespace {
 
@@ -281,6 +282,7 @@ extern "C" const char* ac_status_str(int s) {
 
 extern "C" int ac_build(const char* const* patterns, const uint32_t* lens, uint32_t n_patterns,
                         const ac_build_opts* opts, ac_dfa** out) {
+    AcRange trace_("ac_build");
     if (!out || !patterns || !lens || n_patterns == 0) return AC_ERR_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     const uint32_t flags = opts ? opts->flags : 0u;
@@ -389,6 +391,7 @@ extern "C" int ac_dfa_tables(const ac_dfa* d, ac_dfa_tables_t* o) {
 
 extern "C" int ac_pack(const uint8_t* ascii, uint64_t n, uint32_t* packed, uint32_t flags, uint64_t* bad_offset,
                        void* stream) {
+    AcRange trace_("ac_pack");
     if (bad_offset) *bad_offset = ~0ull;
     if (n == 0) return AC_OK;
     if (!ascii || !packed || (reinterpret_cast<uintptr_t>(packed) & 15)) return AC_ERR_INVALID_ARG;
@@ -686,6 +689,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
 
 extern "C" int ac_scan(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts, void* stream,
                        ac_scan_stats* stats) {
+    AcRange trace_("ac_scan");
     if (!dfa || !text || !r) return AC_ERR_INVALID_ARG;
     r->bad_offset = ~0ull;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
@@ -957,6 +961,7 @@ int scan_pipelined(const ac_dfa* dfa, const ac_text* text, ac_result* r, const a
 
 extern "C" int ac_scan_failureless(const ac_dfa* dfa, const ac_text* text, ac_result* r, const ac_scan_opts* opts,
                                    void* stream, ac_scan_stats* stats) {
+    AcRange trace_("ac_scan_failureless");
     if (!dfa || !text || !r) return AC_ERR_INVALID_ARG;
     r->bad_offset = ~0ull;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
@@ -1044,6 +1049,7 @@ extern "C" void ac_stream_free(ac_stream* s) {
 
 extern "C" int ac_stream_scan(ac_stream* s, const ac_text* piece, ac_result* r, const ac_scan_opts* opts, void* stream,
                               ac_scan_stats* stats) {
+    AcRange trace_("ac_stream_scan");
     if (!s || !piece || !r) return AC_ERR_INVALID_ARG;
     r->bad_offset = ~0ull;
     const ac_dfa* dfa = s->dfa;
@@ -1120,6 +1126,7 @@ extern "C" void ac_part_set_free(ac_part_set* s) {
 
 extern "C" int ac_build_partitioned(const char* const* patterns, const uint32_t* lens, uint32_t n, uint32_t max_states,
                                     const ac_build_opts* opts, ac_part_set** out) {
+    AcRange trace_("ac_build_partitioned");
     if (!patterns || !lens || n == 0 || !out) return AC_ERR_INVALID_ARG;
     const uint32_t cap = max_states ? max_states : ac_max_hot_states(ac_max_threads(1), 1);
     if (cap < 2) return AC_ERR_INVALID_ARG;
@@ -1198,6 +1205,7 @@ extern "C" int ac_part_set_info(const ac_part_set* s, uint32_t* n_parts, uint32_
 
 extern "C" int ac_scan_partitioned(const ac_part_set* set, const ac_text* text, ac_result* r,
                                    const ac_scan_opts* opts, void* stream, ac_scan_stats* stats) {
+    AcRange trace_("ac_scan_partitioned");
     if (!set || !text || !r) return AC_ERR_INVALID_ARG;
     r->bad_offset = ~0ull;
     if (text->encoding != AC_TEXT_ASCII && text->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
@@ -1349,6 +1357,7 @@ int make_prefix(const std::vector<uint64_t>& lens, uint32_t chunk, std::vector<u
 
 extern "C" int ac_scan_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* r,
                              const ac_scan_opts* opts, void* stream, ac_scan_stats* stats) {
+    AcRange trace_("ac_scan_batch");
     if (!dfa || !r || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
     r->bad_offset = ~0ull;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
@@ -1531,6 +1540,7 @@ extern "C" void ac_batch_plan_free(ac_batch_plan* p) {
 
 extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_result* r,
                                     const ac_scan_opts* opts, void* stream, ac_batch_plan** out) {
+    AcRange trace_("ac_batch_plan_create");
     if (!dfa || !r || !out || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (!r->on_device || (r->capacity && !r->matches)) return AC_ERR_INVALID_ARG;
@@ -1635,6 +1645,7 @@ extern "C" int ac_batch_plan_create(const ac_dfa* dfa, const ac_text* texts, uin
 }
 
 extern "C" int ac_batch_plan_run(ac_batch_plan* p, void* stream, int sync, ac_result* r) {
+    AcRange trace_("ac_batch_plan_run");
     if (!p) return AC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGraphLaunch(p->exec, st);

@@ -46,6 +46,7 @@
 #include <vector>
 
 #include "ac_internal.h"
+#include "ac_trace.h"
 
 namespace {
 
@@ -313,6 +314,7 @@ struct ac_server {
 
 void ac_server::run_batch(cudaStream_t st, std::vector<std::shared_ptr<Request>>& batch, PinnedBuf& stage,
                           PinnedBuf& results) {
+    AcRange trace_("ac_serve batch");
     const ac_dfa* dfa = dfas[batch[0]->slot];
     const uint32_t P = dfa->host.n_patterns;
     // ASCII requests first (one pack over their contiguous slots), packed after
@@ -647,6 +649,7 @@ extern "C" int ac_serve_add_dfa(ac_server* s, const ac_dfa* dfa, uint32_t* slot)
 }
 
 extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, uint64_t* ticket) {
+    AcRange trace_("ac_serve_submit");
     if (!s || !t || !ticket) return AC_ERR_INVALID_ARG;
     if (t->on_device) return AC_ERR_INVALID_ARG;
     if (t->encoding != AC_TEXT_ASCII && t->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
@@ -701,6 +704,7 @@ extern "C" int ac_serve_submit(ac_server* s, uint32_t slot, const ac_text* t, ui
 }
 
 extern "C" int ac_serve_wait(ac_server* s, uint64_t ticket, ac_result* res, int64_t timeout_us) {
+    AcRange trace_("ac_serve_wait");
     if (!s || !res) return AC_ERR_INVALID_ARG;
     if (res->on_device || (res->capacity && !res->matches)) return AC_ERR_INVALID_ARG;
     std::shared_ptr<Request> r;
@@ -733,6 +737,7 @@ struct Taken {  // what an ac_serve_take handle owns
 }  // namespace
 
 extern "C" int ac_serve_take(ac_server* s, uint64_t ticket, ac_served* out, int64_t timeout_us) {
+    AcRange trace_("ac_serve_take");
     if (!s || !out) return AC_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof *out);
     std::shared_ptr<Request> r;

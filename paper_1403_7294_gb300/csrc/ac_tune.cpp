@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "ac_internal.h"
+#include "ac_trace.h"
 
 namespace {
 
@@ -230,6 +231,7 @@ int size_output(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, bool 
 }  // namespace
 
 extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opts* best, void* stream) {
+    AcRange trace_("ac_autotune");
     if (!dfa || !sample || !best) return AC_ERR_INVALID_ARG;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     if (!sample->on_device || sample->encoding != AC_TEXT_PACKED2) return AC_ERR_INVALID_ARG;
@@ -343,6 +345,7 @@ extern "C" int ac_autotune(const ac_dfa* dfa, const ac_text* sample, ac_scan_opt
 
 extern "C" int ac_autotune_batch(const ac_dfa* dfa, const ac_text* texts, uint32_t n_texts, ac_scan_opts* best,
                                  void* stream) {
+    AcRange trace_("ac_autotune_batch");
     if (!dfa || !best || (n_texts && !texts)) return AC_ERR_INVALID_ARG;
     if (!dfa->on_device) return AC_ERR_NO_DEVICE;
     uint64_t total = 0;
