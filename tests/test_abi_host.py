@@ -439,3 +439,11 @@ def test_binding_structs_match_the_c_header(tmp_path):
         assert got[(py, "size")] == ctypes.sizeof(cls), py
         for name, _ in cls._fields_:
             assert got[(py, name)] == getattr(cls, name).offset, (py, name)
+
+
+def test_library_carries_its_nvtx_ranges():
+    """The entry points open NVTX ranges in the acgpu domain (names compiled into libac.so)."""
+    blob = open(N.LIB_PATH, "rb").read()
+    for name in (b"acgpu", b"ac_scan", b"ac_scan_batch", b"ac_batch_plan_run", b"ac_stream_scan",
+                 b"ac_serve batch", b"ac_autotune"):
+        assert name + b"\x00" in blob, name
